@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Benchmark of the permutation-index hot path on one GB300 (or N replicas).
+
+A step is one pass of the whole path over the 20M x 64-byte dimension table
+and 500M-row Zipf(s=1.0) FK column: count (Q3) -> sort by frequency ->
+remap the fact keys -> reorder the dimension rows -> FK-join probe with
+filter and GROUP BY SUM.  Inputs are seeded synthetic data generated on the
+device; they are resident in HBM when the timed region starts.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the plain restatement of the paper) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G fact rows/s FK-join+agg, skew-remapped vs plain, same GPU; p99 query latency"
+UNIT = "G rows/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=20_000_000, help="dimension rows")
+    p.add_argument("--f", type=int, default=500_000_000, help="fact rows")
+    p.add_argument("--s", type=float, default=1.0, help="Zipf exponent of the timed step")
+    p.add_argument("--width", type=int, default=16, help="int32 columns per dimension row")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--sweep", default="0.0,0.5,1.0,1.5", help="Zipf exponents of the plain-vs-remapped probe sweep")
+    p.add_argument("--sweep-steps", type=int, default=10)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-rows", type=int, default=20_000_000, help="fact rows in the oracle's timed sample")
+    p.add_argument("--ref-rows", type=int, default=4_000_000, help="fact rows per reference-arm step")
+    return p.parse_args()
+
+
+def workload_name(a):
+    return (f"{a.n // 1_000_000}M x {a.width * 4}B dimension rows, {a.f // 1_000_000}M int32 FK Zipf s={a.s}, "
+            f"SUM(measure*payload0) GROUP BY attr0 WHERE attr1<50")
+
+
+def config_of(a, world):
+    return {"workload": workload_name(a), "N": a.n, "F": a.f, "zipf_s": a.s, "row_bytes": a.width * 4,
+            "num_groups": 1000, "filter": "attr1 < 50", "accumulate": "int64", "seed": a.seed,
+            "l2": "flushed before every timed step (512 MB write, outside the timed events); "
+                  "fact inputs (4 GB/step) are also far larger than L2",
+            "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"}
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_PATH) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def expected_distinct(n, f, s):
+    """E[#distinct keys among f Zipf(s) draws over n keys] = sum_r 1 - (1 - p_r)^f."""
+    from paper_1910_10063_gb300 import synth
+    cdf = synth.zipf_cdf(n, s)
+    p = np.diff(np.concatenate([[0.0], cdf]))
+    return float(np.sum(-np.expm1(f * np.log1p(-np.minimum(p, 1 - 1e-16)))))
+
+
+def source_sha(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    try:
+        with open(TRAFFIC_PATH) as fh:
+            rec = json.load(fh)[kernel_key]
+        src = os.path.join(ROOT, rec["source"])
+        if source_sha(src) != rec["source_sha"]:
+            return None
+        return rec["bytes_per_launch"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.samples = []
+        if self.proc is None:
+            return False
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.samples.append(f)
+        return False
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return None
+        sm = [float(f[1]) for f in self.samples if f[1].replace(".", "").isdigit()]
+        mx = [float(f[2]) for f in self.samples if f[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for f in self.samples for i in range(4) if f[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ====================================================================== ours
+def run_ours(a, rank, world, local_rank):
+    import torch
+    import paper_1910_10063_gb300 as skx
+    from paper_1910_10063_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    q = skx.Query.groupby_sum(num_groups=1000, filter_col=1, filter_lt=50, group_col=0, payload_col=2)
+    w = synth.DeviceWorkload(a.n, a.f, a.s, seed=a.seed, width=a.width, device=dev)
+    fk2 = torch.empty_like(w.fk)
+    dim2 = torch.empty_like(w.dim)
+    counts = torch.empty(a.n, dtype=torch.int32, device=dev)
+    out = torch.empty(1000, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    stages = ["count", "sort", "remap", "reorder", "probe"]
+
+    def step(ev):
+        ev[0].record(stream)
+        skx.skx_count(w.fk, a.n, counts)
+        ev[1].record(stream)
+        idx = skx.skx_build_index_from_counts(counts, a.f)
+        ev[2].record(stream)
+        skx.skx_remap(idx, w.fk, fk2)
+        ev[3].record(stream)
+        skx.skx_reorder(idx, w.dim, dim2)
+        ev[4].record(stream)
+        skx.skx_probe_aggregate(dim2, fk2, w.measure, q, out=out)
+        ev[5].record(stream)
+        return idx
+
+    def new_events():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        step(new_events()).close()
+    st = skx.skx_stream_status()
+    if st != skx.SKX_OK:
+        raise RuntimeError(f"device status {st} during warm-up")
+
+    evs = [new_events() for _ in range(a.steps)]
+    keep = []
+    torch.cuda.synchronize()
+    barrier()
+    launches0 = skx.skx_kernel_launches()
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        for k in range(a.steps):
+            flush.zero_()
+            keep.append(step(evs[k]))
+        torch.cuda.synchronize()
+        region_s = time.perf_counter() - t0
+    barrier()
+    launches = skx.skx_kernel_launches() - launches0
+    for idx in keep:
+        idx.close()
+    step_ms = [e[0].elapsed_time(e[5]) for e in evs]
+    stage_ms = {s: [e[i].elapsed_time(e[i + 1]) for e in evs] for i, s in enumerate(stages)}
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    result = out.cpu().numpy().copy()
+
+    # ---------------- roofline of the dominant kernel
+    peak, peak_src = hbm_peak()
+    D = expected_distinct(a.n, a.f, a.s)
+    row_b = a.width * 4
+    alg = {"count": 4 * a.f + 4 * a.n, "sort": 12 * a.n, "remap": 8 * a.f + 4 * a.n,
+           "reorder": 2 * row_b * a.n + 4 * a.n, "probe": 8 * a.f + 16 * D}
+    kernel_of = {"count": "k_histogram", "sort": "k_radix_*", "remap": "k_remap", "reorder": "k_reorder",
+                 "probe": "k_probe"}
+    src_of = {"count": "paper_1910_10063_gb300/csrc/histogram.cu", "sort": "paper_1910_10063_gb300/csrc/sort.cu",
+              "remap": "paper_1910_10063_gb300/csrc/remap.cu", "reorder": "paper_1910_10063_gb300/csrc/remap.cu",
+              "probe": "paper_1910_10063_gb300/csrc/probe.cu"}
+    stage_avg = {s: statistics.mean(v) for s, v in stage_ms.items()}
+    stage_rep = {s: {"ms": round(stage_avg[s], 4), "alg_bytes": int(alg[s]),
+                     "gbs": round(alg[s] / (stage_avg[s] * 1e-3) / 1e9, 1),
+                     "frac": round(alg[s] / (stage_avg[s] * 1e-3) / 1e9 / peak, 4),
+                     "kernel": kernel_of[s]} for s in stages}
+    dom = max(stages, key=lambda s: stage_avg[s])
+    achieved = alg[dom] / (stage_avg[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kernel_of[dom], "stage": dom, "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} hbm_gbs",
+                "alg_bytes_per_launch": int(alg[dom]), "traffic": ncu_traffic(kernel_of[dom]),
+                "algorithmic_bytes": {"count": "4F + 4N", "sort": "12N (read counts, write perm and rank)",
+                                      "remap": "8F + 4N", "reorder": "2*row_bytes*N + 4N",
+                                      "probe": f"8F + 16*D, D = expected distinct keys = {D:.4g}"}[dom]}
+
+    # ---------------- plain vs remapped probe sweep over the skew
+    sweep = []
+    probe_lat = []
+    if a.sweep and rank == 0:
+        for s in [float(x) for x in a.sweep.split(",") if x.strip()]:
+            ws = synth.DeviceWorkload(a.n, a.f, s, seed=a.seed, width=a.width, device=dev, r2id=w.r2id_host,
+                                      with_measure=False, with_dim=False) if s != a.s else None
+            fk_s = ws.fk if ws is not None else w.fk
+            idx = skx.skx_build_index(fk_s, a.n)
+            skx.skx_remap(idx, fk_s, fk2)
+            skx.skx_reorder(idx, w.dim, dim2)
+            variants = {"plain": (w.dim, fk_s, skx.Tuning.plain()),
+                        "remapped_no_hot_prefix": (dim2, fk2, skx.Tuning.plain()),
+                        "remapped": (dim2, fk2, None)}
+            res, times = {}, {}
+            for name, (rows, keys, tun) in variants.items():
+                o = torch.empty(1000, dtype=torch.int64, device=dev)
+                for _ in range(2):
+                    flush.zero_()
+                    skx.skx_probe_aggregate(rows, keys, w.measure, q, out=o, tuning=tun)
+                ms = []
+                for _ in range(a.sweep_steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    skx.skx_probe_aggregate(rows, keys, w.measure, q, out=o, tuning=tun)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                res[name] = o.cpu().numpy()
+                times[name] = ms
+            idx.close()
+            same = all(np.array_equal(res["plain"], r) for r in res.values())
+            Ds = expected_distinct(a.n, a.f, s)
+            entry = {"zipf_s": s, "results_identical": bool(same), "alg_bytes_per_row": round((8 * a.f + 16 * Ds) / a.f, 3)}
+            for name, ms in times.items():
+                med = statistics.median(ms)
+                gbs = (8 * a.f + 16 * Ds) / (med * 1e-3) / 1e9
+                entry[name] = {"ms": round(med, 4), "grows_s": round(a.f / (med * 1e-3) / 1e9, 2),
+                               "frac_hbm": round(gbs / peak, 4)}
+            entry["speedup_remapped_vs_plain"] = round(entry["plain"]["ms"] / entry["remapped"]["ms"], 3)
+            entry["speedup_layout_only"] = round(entry["plain"]["ms"] / entry["remapped_no_hot_prefix"]["ms"], 3)
+            sweep.append(entry)
+            if s == a.s:
+                probe_lat = times["remapped"]
+            if ws is not None:
+                del ws
+            torch.cuda.empty_cache()
+        st = skx.skx_stream_status()
+        if st != skx.SKX_OK:
+            raise RuntimeError(f"device status {st} during the sweep")
+
+    # ---------------- end to end through the host-buffer C-ABI call
+    e2e = None
+    if not a.no_e2e:
+        h_dim = torch.empty(w.dim.shape, dtype=torch.int32, pin_memory=True)
+        h_fk = torch.empty(a.f, dtype=torch.int32, pin_memory=True)
+        h_m = torch.empty(a.f, dtype=torch.int32, pin_memory=True)
+        h_dim.copy_(w.dim)
+        h_fk.copy_(w.fk)
+        h_m.copy_(w.measure)
+        h_out = np.zeros(1000, dtype=np.int64)
+        del fk2, dim2
+        torch.cuda.empty_cache()
+        skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
+        if not np.array_equal(h_out, result):
+            raise RuntimeError("host-buffer path disagrees with the device-resident path")
+        n_e2e = max(3, min(a.steps, 5))
+        barrier()
+        t = []
+        for _ in range(n_e2e):
+            t0 = time.perf_counter()
+            skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
+            t.append(time.perf_counter() - t0)
+        e2e_s = sum(t)
+        if dist is not None:
+            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": round(world * a.f * n_e2e / e2e_s / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h_dim.numel() * 4 + 2 * a.f * 4), "d2h_bytes_per_step": 8 * 1000,
+               "ms_per_step": round(1e3 * e2e_s / n_e2e, 3), "steps": n_e2e,
+               "api": "skx_join_aggregate_host (pinned host buffers; H2D, build, remap, reorder, probe, D2H)"}
+
+    # ---------------- CPU baseline: the oracle on a bounded sample
+    cpu = None
+    if not a.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(a, fk_host=w.fk[:a.cpu_rows].cpu().numpy(), m_host=w.measure[:a.cpu_rows].cpu().numpy(),
+                           dim_host=w.dim.cpu().numpy())
+
+    if rank != 0:
+        return None
+    value = world * a.f * a.steps / (total_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded Zipf, generated on device)",
+        "config": config_of(a, world), "impl": "ours",
+        "step": "count -> sort by frequency -> remap fk -> reorder dimension -> probe (filter + GROUP BY SUM)",
+        "region_s": round(region_s, 3), "gpu_launches": int(launches),
+        "roofline": roofline, "stages": stage_rep,
+        "probe": {"remapped_p50_ms": round(statistics.median(probe_lat), 4) if probe_lat else None,
+                  "remapped_p99_ms": round(float(np.percentile(probe_lat, 99)), 4) if probe_lat else None,
+                  "sweep": sweep},
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
+    }
+    return line
+
+
+def cpu_baseline(a, fk_host, m_host, dim_host, nthreads=None):
+    """Time the oracle's whole path on a bounded sample (first rows of the fact column)."""
+    import oracle
+    nthreads = nthreads or (os.cpu_count() or 1)
+    t = {}
+    t0 = time.perf_counter()
+    cnt, perm, rank = oracle.build_index(fk_host, dim_host.shape[0])
+    t["build"] = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    fk2 = oracle.remap(rank, fk_host)
+    t["remap"] = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    dim2 = oracle.reorder(perm, dim_host)
+    t["reorder"] = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    oracle.probe(dim2, fk2, m_host, nthreads=nthreads)
+    t["probe"] = time.perf_counter() - t1
+    total = time.perf_counter() - t0
+    rows = fk_host.shape[0]
+    return {"value": round(rows / total / 1e9, 5), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"first {rows} of the {a.f} fact rows with the full {dim_host.shape[0]}-row dimension table; "
+                      f"whole path (count, qsort, invert, remap, reorder single-threaded; probe on {nthreads} threads)",
+            "seconds": {k: round(v, 3) for k, v in t.items()}}
+
+
+# ====================================================================== reference
+def run_reference(a, rank, world):
+    """The oracle, as it stands, on host cores: each step a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1910_10063_gb300 import synth
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    cdf = synth.zipf_cdf(a.n, a.s)
+    r2id = synth.rank_to_id(a.n, a.seed)
+    dim = synth.dim_rows_host(a.n, a.width, a.seed)
+    rows = min(a.ref_rows, a.f)
+
+    def one(k):
+        start = (k * rows) % max(1, a.f - rows + 1)
+        fk = synth.zipf_fk_host(cdf, r2id, a.seed, start, rows)
+        m = synth.measure_host(a.seed, start, rows)
+        t0 = time.perf_counter()
+        cnt, perm, rank_ = oracle.build_index(fk, a.n)
+        fk2 = oracle.remap(rank_, fk)
+        dim2 = oracle.reorder(perm, dim)
+        oracle.probe(dim2, fk2, m, nthreads=nthreads)
+        return time.perf_counter() - t0
+
+    for k in range(a.warmup):
+        one(k)
+    times = [one(a.warmup + k) for k in range(a.steps)]
+    total = sum(times)
+    value = rows * a.steps / total / 1e9
+    sample = (f"{rows} consecutive fact rows per step (of {a.f}) with the full {a.n}-row dimension table; "
+              f"whole path (count, qsort, invert, remap, reorder single-threaded; probe on {nthreads} threads)")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * total / a.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded Zipf, host generator)", "config": config_of(a, world),
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != a.gpus and world != 1:
+        raise SystemExit(f"--gpus {a.gpus} but WORLD_SIZE={world}")
+    if a.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if a.impl == "reference":
+        line = run_reference(a, rank, world)
+    else:
+        line = run_ours(a, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

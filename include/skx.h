@@ -1,0 +1,210 @@
+/*
+ * skx.h -- C ABI of the GB300 permutation-index library (libskx.so).
+ *
+ * The permutation index of Zhang & Ross, "Exploiting Data Skew for Improved
+ * Query Performance" (ICDE 2020, arXiv 1910.10063): count how often each
+ * foreign key occurs in a fact column, order the dimension rows by that
+ * popularity, and relabel both sides with the resulting permutation so that
+ * popular rows sit together at the front of the dimension table.  Queries
+ * that join through the FK then touch a small, contiguous hot prefix.
+ *
+ * Conventions (all entry points):
+ *   - Data pointers named d_* are DEVICE pointers (cudaMalloc / torch CUDA
+ *     tensors) owned by the caller, on the current CUDA device.  h_* are
+ *     host pointers (pinned memory gives the fastest copies).
+ *   - Columns are dense little-endian int32 arrays; a foreign key is a
+ *     0-based row offset into the dimension table (Section II-B).
+ *   - Dimension tables are row-major records of `row_bytes` bytes
+ *     (a multiple of 4); column c of a row is the int32 at byte offset 4*c.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; the call returns once
+ *     the work is enqueued.
+ *   - Argument errors are returned synchronously and enqueue nothing.
+ *     Errors found in the data by the kernels (a foreign key outside
+ *     [0, N), a group key outside [0, G)) never fault: the offending row is
+ *     skipped and a per-device error word is set; skx_stream_status()
+ *     reports and clears it.
+ *   - Every output buffer is fully overwritten.
+ *   - Sizes: F (fact rows) up to 2^32 - 1, N (dimension rows) up to 2^31 - 1.
+ */
+#ifndef SKX_H
+#define SKX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SKX_VERSION_MAJOR 1
+#define SKX_VERSION_MINOR 0
+
+typedef enum skx_status {
+    SKX_OK = 0,
+    SKX_EINVAL = 1,      /* bad argument: null pointer, negative or too large size, bad column */
+    SKX_ENOMEM = 2,      /* a device or pinned-host allocation failed */
+    SKX_EKEYRANGE = 3,   /* the data held a foreign key outside [0, N) */
+    SKX_EGROUPRANGE = 4, /* the data held a group key outside [0, G) */
+    SKX_ECUDA = 5,       /* a CUDA runtime call failed (see skx_last_cuda_error) */
+    SKX_ETIMEOUT = 6,    /* a bounded device-side wait expired */
+    SKX_EBUSY = 7,       /* no free slot / resource (serving admission) */
+    SKX_ENOTSUP = 8      /* valid request this build does not support */
+} skx_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *skx_strerror(skx_status s);
+
+/* Message of the last CUDA error seen by this library in this thread. */
+const char *skx_last_cuda_error(void);
+
+/* Library version as (major << 16) | minor. */
+int32_t skx_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all devices, all streams); a diagnostic for counting launches per call. */
+uint64_t skx_kernel_launches(void);
+
+/*
+ * Synchronises `stream`, then reports and clears the per-device data-error
+ * word of the current device: SKX_EKEYRANGE or SKX_EGROUPRANGE if any kernel
+ * of this library on this device met such data since the last call (from any
+ * stream), SKX_ECUDA if the stream itself failed, else SKX_OK.
+ */
+skx_status skx_stream_status(void *stream);
+
+/* ------------------------------------------------------------------------
+ * Index build (Section III and III-A).
+ *
+ * The index is the popularity order of the dimension ids: a count of each
+ * value of the fact column C (the Q3 aggregation), then the ids sorted by
+ * decreasing count.  It is held in both representations of Section III:
+ *   perm[r]  offset representation, new -> old: the id of rank r;
+ *   rank[v]  rank representation,  old -> new: the rank of id v;
+ * so rank[perm[r]] == r.  Ties are broken by ascending id and ids that never
+ * occur follow all others (ascending), so perm is a bijection on [0, N)
+ * and is unique for given data.  counts[v] (uint32) is kept as well.
+ * ------------------------------------------------------------------------ */
+typedef struct skx_index skx_index; /* opaque; owns device memory until destroyed */
+
+/*
+ * Builds the index of the FK column d_fk[F] over dimension ids [0, N).
+ * Allocates the index's arrays (3 * 4 * N bytes) and temporary scratch with
+ * stream-ordered allocation on `stream`; *out receives the handle
+ * immediately, its arrays become valid in stream order.  Keys outside
+ * [0, N) are not counted and raise SKX_EKEYRANGE at skx_stream_status.
+ * Errors: SKX_EINVAL (null d_fk with F > 0, N < 1, F >= 2^32, null out),
+ * SKX_ENOMEM, SKX_ECUDA.
+ */
+skx_status skx_build_index(const int32_t *d_fk, int64_t F, int32_t N, void *stream,
+                           skx_index **out);
+
+/*
+ * The two halves of skx_build_index, for callers that want the Q3 count on its
+ * own (Section I, query Q3; Section III-A, first step).
+ * skx_count: d_counts[v] = #{i : d_fk[i] == v} for v in [0, N) (uint32,
+ * fully overwritten; keys outside [0, N) are skipped and raise SKX_EKEYRANGE).
+ * skx_build_index_from_counts: sorts the ids by (count desc, id asc) and
+ * returns an index that takes a copy of the counts.  F is only an upper
+ * bound on every count (it sets how many key bits are sorted).
+ */
+skx_status skx_count(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_counts, void *stream);
+skx_status skx_build_index_from_counts(const uint32_t *d_counts, int32_t N, int64_t F, void *stream,
+                                       skx_index **out);
+
+/* Borrowed device pointers into the index (valid until skx_index_destroy). */
+skx_status skx_index_perm(const skx_index *idx, const int32_t **d_perm);     /* new -> old, int32[N] */
+skx_status skx_index_rank(const skx_index *idx, const int32_t **d_rank);     /* old -> new, int32[N] */
+skx_status skx_index_counts(const skx_index *idx, const uint32_t **d_counts); /* uint32[N] */
+int32_t skx_index_size(const skx_index *idx);                                /* N, or -1 */
+
+/* Frees the index (stream-ordered on the stream it was built on). NULL is a no-op. */
+void skx_index_destroy(skx_index *idx);
+
+/* ------------------------------------------------------------------------
+ * Recode of the fact column (Section III-A): d_fk_out[i] = rank[d_fk_in[i]].
+ * d_fk_out may equal d_fk_in (in place); other overlaps are not allowed.
+ * Keys outside [0, N) are copied through unchanged and raise SKX_EKEYRANGE.
+ * ------------------------------------------------------------------------ */
+skx_status skx_remap(const skx_index *idx, const int32_t *d_fk_in, int32_t *d_fk_out, int64_t F,
+                     void *stream);
+
+/* ------------------------------------------------------------------------
+ * Permuted copy of the dimension table (Section III-B):
+ * row r of d_rows_out = row perm[r] of d_rows_in, row_bytes bytes each
+ * (a multiple of 4).  Input and output must not overlap.
+ * ------------------------------------------------------------------------ */
+skx_status skx_reorder(const skx_index *idx, const void *d_rows_in, void *d_rows_out, int32_t N,
+                       int32_t row_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * FK-join probe + filter + aggregation (Sections I and IV: the Q1 gather
+ * through the FK, the Q2 filter on a dimension attribute, and aggregation;
+ * Section IV-B threshold processing for the hot prefix).
+ *
+ *   COUNT        out[0] = #{i : row(fk[i]).filter_col < filter_lt}
+ *   SUM          out[0] = sum of measure[i] * row(fk[i]).payload_col over those i
+ *   GROUPBY_SUM  out[g] = the same sum restricted to row(fk[i]).group_col == g,
+ *                for g in [0, num_groups)
+ *
+ * Products are formed in int64 and sums wrap modulo 2^64 (bit-exact, order
+ * free).  filter_col = -1 disables the filter; payload_col = -1 uses payload
+ * 1 (SUM(measure)).  d_measure may be NULL for COUNT.
+ *
+ * The call is layout agnostic: on (plain rows, original keys) and on
+ * (skx_reorder'ed rows, skx_remap'ped keys) it returns identical results.
+ * With a remapped layout, rows [0, hot_keys) -- the most popular -- are
+ * aggregated per key in shared memory without touching the dimension table
+ * until the end of each CTA (threshold-based processing of Section IV-B).
+ * ------------------------------------------------------------------------ */
+typedef enum skx_agg { SKX_AGG_COUNT = 0, SKX_AGG_SUM = 1, SKX_AGG_GROUPBY_SUM = 2 } skx_agg;
+
+typedef struct skx_query {
+    int32_t agg;         /* skx_agg */
+    int32_t filter_col;  /* column tested with "< filter_lt", or -1 for no filter */
+    int32_t filter_lt;
+    int32_t group_col;   /* GROUPBY_SUM only */
+    int32_t num_groups;  /* G, GROUPBY_SUM only, 1 .. 2^24 */
+    int32_t payload_col; /* column multiplied with the measure, or -1 for 1 */
+} skx_query;
+
+/* Launch and threshold parameters; zero-initialise and set what you need.
+ * A field left at 0 takes the library default (chosen from N, F and the
+ * device); hot_keys = -1 disables the hot prefix (plain processing). */
+typedef struct skx_tuning {
+    int32_t block_threads; /* 128, 256 or 512 */
+    int32_t ctas_per_sm;   /* resident CTAs per SM targeted by the persistent grid */
+    int32_t hot_keys;      /* t: keys [0, t) aggregated per key in shared memory; -1 = off */
+    int32_t lane_keys;     /* keys [0, t_lane) (t_lane <= t) get one copy per warp lane; -1 = off */
+    int32_t warp_aggregate;/* 1: merge equal group keys within a warp before the atomic; -1 = off */
+    int32_t unroll;        /* 16-byte vectors per thread per iteration: 1, 2 or 4 */
+    int32_t reserved[10];
+} skx_tuning;
+
+skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
+                               const int32_t *d_measure, int64_t F, const skx_query *q, int64_t *d_out,
+                               const skx_tuning *tuning /* NULL = defaults */, void *stream);
+
+/* The tuning skx_probe_aggregate would use for these arguments (defaults or
+ * the autotuner's cached choice), written to *out. */
+skx_status skx_probe_default_tuning(int32_t N, int32_t row_bytes, int64_t F, const skx_query *q,
+                                    int remapped, skx_tuning *out);
+
+/* ------------------------------------------------------------------------
+ * Whole path from host memory (Sections III-A, III-B and IV in sequence):
+ * copies h_fk[F], h_measure[F] and the dimension table h_rows[N * row_bytes]
+ * to the device, builds the index, remaps the keys, reorders the rows,
+ * runs the query on the reordered layout and copies the result (num_groups
+ * or 1 int64) to h_out.  Device buffers are stream-ordered allocations on
+ * `stream`, released before return.  Synchronous: returns after h_out is
+ * written, with any data error of this call already reported (SKX_EKEYRANGE,
+ * SKX_EGROUPRANGE) rather than left for skx_stream_status.
+ * ------------------------------------------------------------------------ */
+skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_bytes, const int32_t *h_fk,
+                                   const int32_t *h_measure, int64_t F, const skx_query *q,
+                                   int64_t *h_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKX_H */

@@ -1,0 +1,320 @@
+"""GB300 permutation index (Zhang & Ross, ICDE 2020, arXiv 1910.10063).
+
+Thin ctypes binding over ``libskx.so`` (C ABI in ``include/skx.h``).  The
+functions below carry the C entry points' names and only marshal arguments:
+torch CUDA tensors supply device pointers, the current torch stream supplies
+the CUDA stream, and every step of the path runs in the library's kernels.
+There is no CPU fallback: without the built library every call raises.
+
+    import torch, paper_1910_10063_gb300 as skx
+    idx = skx.skx_build_index(fk, N)                  # Section III-A: count + sort
+    fk2 = torch.empty_like(fk); skx.skx_remap(idx, fk, fk2)
+    dim2 = torch.empty_like(dim); skx.skx_reorder(idx, dim, dim2)
+    out = skx.skx_probe_aggregate(dim2, fk2, measure, skx.Query.groupby_sum())
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libskx.so")
+
+SKX_OK, SKX_EINVAL, SKX_ENOMEM, SKX_EKEYRANGE, SKX_EGROUPRANGE = 0, 1, 2, 3, 4
+SKX_ECUDA, SKX_ETIMEOUT, SKX_EBUSY, SKX_ENOTSUP = 5, 6, 7, 8
+SKX_AGG_COUNT, SKX_AGG_SUM, SKX_AGG_GROUPBY_SUM = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SkxError(RuntimeError):
+    def __init__(self, status: int, where: str, lib=None):
+        msg = f"{where}: status {status}"
+        if lib is not None:
+            msg = f"{where}: {lib.skx_strerror(status).decode()}"
+            if status == SKX_ECUDA:
+                msg += f" ({lib.skx_last_cuda_error().decode()})"
+        super().__init__(msg)
+        self.status = status
+
+
+class Query(ctypes.Structure):
+    _fields_ = [("agg", ctypes.c_int32), ("filter_col", ctypes.c_int32), ("filter_lt", ctypes.c_int32),
+                ("group_col", ctypes.c_int32), ("num_groups", ctypes.c_int32), ("payload_col", ctypes.c_int32)]
+
+    @classmethod
+    def groupby_sum(cls, num_groups=1000, filter_col=1, filter_lt=50, group_col=0, payload_col=2):
+        return cls(SKX_AGG_GROUPBY_SUM, filter_col, filter_lt, group_col, num_groups, payload_col)
+
+    @classmethod
+    def sum(cls, filter_col=1, filter_lt=50, payload_col=2):
+        return cls(SKX_AGG_SUM, filter_col, filter_lt, 0, 1, payload_col)
+
+    @classmethod
+    def count(cls, filter_col=1, filter_lt=50):
+        return cls(SKX_AGG_COUNT, filter_col, filter_lt, 0, 1, -1)
+
+    @property
+    def nout(self) -> int:
+        return self.num_groups if self.agg == SKX_AGG_GROUPBY_SUM else 1
+
+    def __repr__(self):
+        return (f"Query(agg={self.agg}, filter_col={self.filter_col}, filter_lt={self.filter_lt}, "
+                f"group_col={self.group_col}, num_groups={self.num_groups}, payload_col={self.payload_col})")
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("hot_keys", ctypes.c_int32),
+                ("lane_keys", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32), ("unroll", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+    @classmethod
+    def plain(cls):
+        """No hot prefix: the probe used on a layout without a permutation index."""
+        t = cls()
+        t.hot_keys = -1
+        t.lane_keys = -1
+        return t
+
+    def __repr__(self):
+        return f"Tuning({self.as_dict()})"
+
+
+def lib():
+    """Load libskx.so (raises if it has not been built -- there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libskx.so is not built at {LIB_PATH}; run "
+                                   "`python -m paper_1910_10063_gb300.build` (needs nvcc)")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            st = ctypes.c_int
+            L.skx_strerror.argtypes = [st]; L.skx_strerror.restype = ctypes.c_char_p
+            L.skx_last_cuda_error.argtypes = []; L.skx_last_cuda_error.restype = ctypes.c_char_p
+            L.skx_version.argtypes = []; L.skx_version.restype = i32
+            L.skx_stream_status.argtypes = [P]; L.skx_stream_status.restype = st
+            L.skx_build_index.argtypes = [P, i64, i32, P, ctypes.POINTER(P)]; L.skx_build_index.restype = st
+            L.skx_count.argtypes = [P, i64, i32, P, P]; L.skx_count.restype = st
+            L.skx_build_index_from_counts.argtypes = [P, i32, i64, P, ctypes.POINTER(P)]
+            L.skx_build_index_from_counts.restype = st
+            L.skx_kernel_launches.argtypes = []; L.skx_kernel_launches.restype = ctypes.c_uint64
+            for n in ("skx_index_perm", "skx_index_rank", "skx_index_counts"):
+                getattr(L, n).argtypes = [P, ctypes.POINTER(P)]
+                getattr(L, n).restype = st
+            L.skx_index_size.argtypes = [P]; L.skx_index_size.restype = i32
+            L.skx_index_destroy.argtypes = [P]; L.skx_index_destroy.restype = None
+            L.skx_remap.argtypes = [P, P, P, i64, P]; L.skx_remap.restype = st
+            L.skx_reorder.argtypes = [P, P, P, i32, i32, P]; L.skx_reorder.restype = st
+            L.skx_probe_aggregate.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), P,
+                                              ctypes.POINTER(Tuning), P]
+            L.skx_probe_aggregate.restype = st
+            L.skx_probe_default_tuning.argtypes = [i32, i32, i64, ctypes.POINTER(Query), ctypes.c_int,
+                                                   ctypes.POINTER(Tuning)]
+            L.skx_probe_default_tuning.restype = st
+            L.skx_join_aggregate_host.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), P, P]
+            L.skx_join_aggregate_host.restype = st
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != SKX_OK:
+        raise SkxError(status, where, lib())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(t, what, dtype=None):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Index:
+    """Owner of an ``skx_index`` (perm, rank and counts on the device)."""
+
+    def __init__(self, handle: ctypes.c_void_p, n: int):
+        self._h = handle
+        self.n = n
+
+    def _view(self, fn, dtype):
+        import torch
+        p = ctypes.c_void_p()
+        _check(getattr(lib(), fn)(self._h, ctypes.byref(p)), fn)
+        return _device_view(p.value, self.n, dtype)
+
+    @property
+    def perm(self):
+        """int32[N] new -> old (borrowed view, valid while the Index lives)."""
+        import torch
+        return self._view("skx_index_perm", torch.int32)
+
+    @property
+    def rank(self):
+        """int32[N] old -> new (borrowed view)."""
+        import torch
+        return self._view("skx_index_rank", torch.int32)
+
+    @property
+    def counts(self):
+        """uint32 counts viewed as int32[N] (borrowed view)."""
+        import torch
+        return self._view("skx_index_counts", torch.int32)
+
+    def close(self):
+        if self._h:
+            lib().skx_index_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _device_view(ptr: int, n: int, dtype):
+    """A torch tensor over library-owned device memory (no copy, no ownership)."""
+    import torch
+    itemsize = torch.empty((), dtype=dtype).element_size()
+
+    class _Holder:
+        pass
+
+    h = _Holder()
+    h.__cuda_array_interface__ = {"shape": (n,), "typestr": {1: "|i1", 4: "<i4", 8: "<i8"}[itemsize],
+                                  "data": (ptr, False), "version": 3, "strides": None}
+    return torch.as_tensor(h, device="cuda").view(dtype)
+
+
+# ------------------------------------------------------------------ entry points
+def skx_version() -> int:
+    return lib().skx_version()
+
+
+def skx_stream_status(stream=None) -> int:
+    """Synchronise and return (and clear) the data-error status; see skx.h."""
+    return lib().skx_stream_status(_stream(stream))
+
+
+def skx_build_index(fk, n: int, stream=None) -> Index:
+    import torch
+    h = ctypes.c_void_p()
+    _check(lib().skx_build_index(_dptr(fk, "fk", torch.int32), fk.numel(), int(n), _stream(stream), ctypes.byref(h)),
+           "skx_build_index")
+    return Index(h, int(n))
+
+
+def skx_count(fk, n: int, counts=None, stream=None):
+    """Q3 count: int32 view of uint32 counts[n] on the device."""
+    import torch
+    if counts is None:
+        counts = torch.empty(n, dtype=torch.int32, device=fk.device)
+    _check(lib().skx_count(_dptr(fk, "fk", torch.int32), fk.numel(), int(n), _dptr(counts, "counts", torch.int32),
+                           _stream(stream)), "skx_count")
+    return counts
+
+
+def skx_build_index_from_counts(counts, f_bound: int, stream=None) -> Index:
+    import torch
+    h = ctypes.c_void_p()
+    _check(lib().skx_build_index_from_counts(_dptr(counts, "counts", torch.int32), counts.numel(), int(f_bound),
+                                             _stream(stream), ctypes.byref(h)), "skx_build_index_from_counts")
+    return Index(h, counts.numel())
+
+
+def skx_kernel_launches() -> int:
+    return lib().skx_kernel_launches()
+
+
+def skx_remap(index: Index, fk_in, fk_out, stream=None):
+    import torch
+    if fk_out.numel() != fk_in.numel():
+        raise ValueError("fk_out must have the same length as fk_in")
+    _check(lib().skx_remap(index._h, _dptr(fk_in, "fk_in", torch.int32), _dptr(fk_out, "fk_out", torch.int32),
+                           fk_in.numel(), _stream(stream)), "skx_remap")
+    return fk_out
+
+
+def _row_bytes(rows):
+    if rows.dim() < 1 or rows.shape[0] == 0:
+        raise ValueError("rows must have a leading row dimension")
+    return rows.numel() * rows.element_size() // rows.shape[0]
+
+
+def skx_reorder(index: Index, rows_in, rows_out, stream=None):
+    if rows_out.shape != rows_in.shape or rows_out.dtype != rows_in.dtype:
+        raise ValueError("rows_out must match rows_in")
+    _check(lib().skx_reorder(index._h, _dptr(rows_in, "rows_in"), _dptr(rows_out, "rows_out"), rows_in.shape[0],
+                             _row_bytes(rows_in), _stream(stream)), "skx_reorder")
+    return rows_out
+
+
+def skx_probe_aggregate(rows, fk, measure, query: Query, out=None, tuning: Tuning | None = None, stream=None):
+    """int64 result tensor ([num_groups] for GROUPBY_SUM, [1] otherwise) on the device."""
+    import torch
+    if out is None:
+        out = torch.empty(query.nout, dtype=torch.int64, device=fk.device)
+    if measure is not None and measure.numel() != fk.numel():
+        raise ValueError("measure must have the same length as fk")
+    _check(lib().skx_probe_aggregate(_dptr(rows, "rows"), rows.shape[0], _row_bytes(rows),
+                                     _dptr(fk, "fk", torch.int32), _dptr(measure, "measure", torch.int32),
+                                     fk.numel(), ctypes.byref(query), _dptr(out, "out", torch.int64),
+                                     ctypes.byref(tuning) if tuning is not None else None, _stream(stream)),
+           "skx_probe_aggregate")
+    return out
+
+
+def skx_probe_default_tuning(n: int, row_bytes: int, f: int, query: Query, remapped: bool = True) -> Tuning:
+    t = Tuning()
+    _check(lib().skx_probe_default_tuning(n, row_bytes, f, ctypes.byref(query), int(remapped), ctypes.byref(t)),
+           "skx_probe_default_tuning")
+    return t
+
+
+def skx_join_aggregate_host(rows, fk, measure, query: Query, out=None, stream=None):
+    """Whole path from host memory (numpy arrays or CPU tensors, pinned is fastest)."""
+    import numpy as np
+    import torch
+
+    def hptr(a, what):
+        if a is None:
+            return None, 0
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError(f"{what} must be a contiguous host tensor")
+            return ctypes.c_void_p(a.data_ptr()), a
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data_as(ctypes.c_void_p), a
+
+    prow, rows_keep = hptr(rows, "rows")
+    pfk, fk_keep = hptr(fk, "fk")
+    pm, m_keep = hptr(measure, "measure")
+    n = rows.shape[0]
+    row_bytes = (rows.numel() * rows.element_size() if isinstance(rows, torch.Tensor) else rows.nbytes) // n
+    nf = fk.numel() if isinstance(fk, torch.Tensor) else np.asarray(fk).size
+    if out is None:
+        out = np.zeros(query.nout, dtype=np.int64)
+    pout, out_keep = hptr(out, "out")
+    _check(lib().skx_join_aggregate_host(prow, n, row_bytes, pfk, pm, nf, ctypes.byref(query), pout, _stream(stream)),
+           "skx_join_aggregate_host")
+    return out_keep

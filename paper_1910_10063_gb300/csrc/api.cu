@@ -1,0 +1,353 @@
+// api.cu -- the extern "C" boundary of libskx (declared in include/skx.h).
+// Argument checking, the index object, stream-ordered allocation and the
+// per-device data-error word; every step of the path runs in the kernels of
+// histogram.cu, sort.cu, remap.cu and probe.cu.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "skx_internal.cuh"
+
+struct skx_index {
+    int device;
+    int32_t N;
+    int64_t F;
+    cudaStream_t stream;  // stream the arrays were allocated on (freed there)
+    uint32_t *counts;
+    int32_t *perm;
+    int32_t *rank;
+};
+
+namespace skx {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned *g_err_word[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
+int g_smem_optin[kMaxDevices] = {};
+thread_local char g_last_cuda[256] = "no CUDA error";
+std::atomic<uint64_t> g_launches{0};
+
+int current_device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return 0;
+    return d;
+}
+
+void query_device(int d) {
+    if (g_sms[d] > 0) return;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+    g_sms[d] = v > 0 ? v : 1;
+    v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+    g_smem_optin[d] = v > 0 ? v : 48 * 1024;
+    // keep freed stream-ordered allocations in the device pool between calls
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+}
+
+bool valid_stream_ptrs(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+
+}  // namespace
+
+void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+skx_status cuda_status(cudaError_t e) {
+    snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return SKX_ENOMEM;
+    return SKX_ECUDA;
+}
+
+unsigned *device_error_word() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_err_word[d]) {
+        unsigned *w = nullptr;
+        if (cudaMalloc(&w, sizeof(unsigned)) != cudaSuccess) return nullptr;
+        cudaMemset(w, 0, sizeof(unsigned));
+        cudaDeviceSynchronize();
+        g_err_word[d] = w;
+    }
+    return g_err_word[d];
+}
+
+int device_sm_count() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    query_device(d);
+    return g_sms[d];
+}
+
+int device_max_smem_optin() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    query_device(d);
+    return g_smem_optin[d];
+}
+
+}  // namespace skx
+
+using namespace skx;
+
+namespace {
+
+// Allocates an index whose counts are written by `fill` (a histogram or a copy),
+// then sorts.  On failure everything is released.
+template <typename Fill>
+skx_status make_index(int32_t N, int64_t F, cudaStream_t st, skx_index **out, Fill fill) {
+    skx_index *idx = new skx_index{};
+    idx->device = 0;
+    cudaGetDevice(&idx->device);
+    idx->N = N;
+    idx->F = F;
+    idx->stream = st;
+    const size_t nb = size_t(N) * 4;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&idx->counts), nb, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&idx->perm), nb, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&idx->rank), nb, st);
+    void *scratch = nullptr;
+    const size_t sb = sort_scratch_bytes(N, F);
+    if (e == cudaSuccess && sb) e = cudaMallocAsync(&scratch, sb, st);
+    if (e == cudaSuccess) e = fill(idx->counts);
+    if (e == cudaSuccess) e = launch_sort_by_count(idx->counts, N, F, idx->perm, idx->rank, scratch, sb, st);
+    if (scratch) cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) {
+        skx_status s = cuda_status(e);
+        skx_index_destroy(idx);
+        return s;
+    }
+    *out = idx;
+    return SKX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *skx_strerror(skx_status s) {
+    switch (s) {
+        case SKX_OK: return "SKX_OK";
+        case SKX_EINVAL: return "SKX_EINVAL: invalid argument";
+        case SKX_ENOMEM: return "SKX_ENOMEM: out of memory";
+        case SKX_EKEYRANGE: return "SKX_EKEYRANGE: foreign key outside [0, N)";
+        case SKX_EGROUPRANGE: return "SKX_EGROUPRANGE: group key outside [0, G)";
+        case SKX_ECUDA: return "SKX_ECUDA: CUDA error";
+        case SKX_ETIMEOUT: return "SKX_ETIMEOUT: bounded wait expired";
+        case SKX_EBUSY: return "SKX_EBUSY: resource busy";
+        case SKX_ENOTSUP: return "SKX_ENOTSUP: not supported";
+    }
+    return "SKX_?: unknown status";
+}
+
+const char *skx_last_cuda_error(void) { return g_last_cuda; }
+
+int32_t skx_version(void) { return (SKX_VERSION_MAJOR << 16) | SKX_VERSION_MINOR; }
+
+uint64_t skx_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+skx_status skx_stream_status(void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SKX_CUDA_TRY(cudaStreamSynchronize(st));
+    unsigned *w = device_error_word();
+    if (!w) return SKX_ENOMEM;
+    unsigned h = 0;
+    SKX_CUDA_TRY(cudaMemcpyAsync(&h, w, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SKX_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(unsigned), st));
+    SKX_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h & kErrKeyRange) return SKX_EKEYRANGE;
+    if (h & kErrGroupRange) return SKX_EGROUPRANGE;
+    if (h & kErrTimeout) return SKX_ETIMEOUT;
+    return SKX_OK;
+}
+
+skx_status skx_count(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_counts, void *stream) {
+    if (N < 1 || F < 0 || F >= (int64_t(1) << 32) || (F > 0 && !d_fk) || !d_counts || !valid_stream_ptrs(d_fk) ||
+        !valid_stream_ptrs(d_counts))
+        return SKX_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    SKX_CUDA_TRY(cudaMemsetAsync(d_counts, 0, size_t(N) * 4, st));
+    SKX_CUDA_TRY(launch_histogram(d_fk, F, N, d_counts, err, st));
+    return SKX_OK;
+}
+
+skx_status skx_build_index(const int32_t *d_fk, int64_t F, int32_t N, void *stream, skx_index **out) {
+    if (!out) return SKX_EINVAL;
+    *out = nullptr;
+    if (N < 1 || F < 0 || F >= (int64_t(1) << 32) || (F > 0 && !d_fk) || !valid_stream_ptrs(d_fk)) return SKX_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    return make_index(N, F, st, out, [&](uint32_t *counts) {
+        cudaError_t e = cudaMemsetAsync(counts, 0, size_t(N) * 4, st);
+        if (e == cudaSuccess) e = launch_histogram(d_fk, F, N, counts, err, st);
+        return e;
+    });
+}
+
+skx_status skx_build_index_from_counts(const uint32_t *d_counts, int32_t N, int64_t F, void *stream,
+                                       skx_index **out) {
+    if (!out) return SKX_EINVAL;
+    *out = nullptr;
+    if (N < 1 || F < 0 || F >= (int64_t(1) << 32) || !d_counts || !valid_stream_ptrs(d_counts)) return SKX_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return make_index(N, F, st, out, [&](uint32_t *counts) {
+        return cudaMemcpyAsync(counts, d_counts, size_t(N) * 4, cudaMemcpyDeviceToDevice, st);
+    });
+}
+
+skx_status skx_index_perm(const skx_index *idx, const int32_t **d_perm) {
+    if (!idx || !d_perm) return SKX_EINVAL;
+    *d_perm = idx->perm;
+    return SKX_OK;
+}
+
+skx_status skx_index_rank(const skx_index *idx, const int32_t **d_rank) {
+    if (!idx || !d_rank) return SKX_EINVAL;
+    *d_rank = idx->rank;
+    return SKX_OK;
+}
+
+skx_status skx_index_counts(const skx_index *idx, const uint32_t **d_counts) {
+    if (!idx || !d_counts) return SKX_EINVAL;
+    *d_counts = idx->counts;
+    return SKX_OK;
+}
+
+int32_t skx_index_size(const skx_index *idx) { return idx ? idx->N : -1; }
+
+void skx_index_destroy(skx_index *idx) {
+    if (!idx) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != idx->device) cudaSetDevice(idx->device);
+    if (idx->counts) cudaFreeAsync(idx->counts, idx->stream);
+    if (idx->perm) cudaFreeAsync(idx->perm, idx->stream);
+    if (idx->rank) cudaFreeAsync(idx->rank, idx->stream);
+    if (prev != idx->device) cudaSetDevice(prev);
+    delete idx;
+}
+
+skx_status skx_remap(const skx_index *idx, const int32_t *d_fk_in, int32_t *d_fk_out, int64_t F, void *stream) {
+    if (!idx || F < 0 || (F > 0 && (!d_fk_in || !d_fk_out))) return SKX_EINVAL;
+    if (!valid_stream_ptrs(d_fk_in) || !valid_stream_ptrs(d_fk_out)) return SKX_EINVAL;
+    if (F > 0 && d_fk_in != d_fk_out) {  // partial overlap is not allowed
+        const char *a = reinterpret_cast<const char *>(d_fk_in), *b = reinterpret_cast<const char *>(d_fk_out);
+        if (a < b + F * 4 && b < a + F * 4) return SKX_EINVAL;
+    }
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    SKX_CUDA_TRY(launch_remap(idx->rank, idx->N, d_fk_in, d_fk_out, F, err, static_cast<cudaStream_t>(stream)));
+    return SKX_OK;
+}
+
+skx_status skx_reorder(const skx_index *idx, const void *d_rows_in, void *d_rows_out, int32_t N, int32_t row_bytes,
+                       void *stream) {
+    if (!idx || N != idx->N || row_bytes <= 0 || row_bytes % 4 != 0 || !d_rows_in || !d_rows_out) return SKX_EINVAL;
+    if (!valid_stream_ptrs(d_rows_in) || !valid_stream_ptrs(d_rows_out)) return SKX_EINVAL;
+    const char *a = static_cast<const char *>(d_rows_in), *b = static_cast<const char *>(d_rows_out);
+    const int64_t bytes = int64_t(N) * row_bytes;
+    if (a < b + bytes && b < a + bytes) return SKX_EINVAL;
+    SKX_CUDA_TRY(launch_reorder(idx->perm, N, d_rows_in, d_rows_out, row_bytes, static_cast<cudaStream_t>(stream)));
+    return SKX_OK;
+}
+
+skx_status skx_probe_default_tuning(int32_t N, int32_t row_bytes, int64_t F, const skx_query *q, int remapped,
+                                    skx_tuning *out) {
+    if (!out || N < 1 || F < 0) return SKX_EINVAL;
+    skx_status s = validate_query(q, row_bytes);
+    if (s != SKX_OK) return s;
+    ProbeArgs a{};
+    a.N = N;
+    a.row_bytes = row_bytes;
+    a.F = F;
+    a.q = *q;
+    skx_tuning t{};
+    if (!remapped) t.hot_keys = -1;
+    resolve_probe_tuning(a, t);
+    *out = t;
+    return SKX_OK;
+}
+
+skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
+                               const int32_t *d_measure, int64_t F, const skx_query *q, int64_t *d_out,
+                               const skx_tuning *tuning, void *stream) {
+    skx_status s = validate_query(q, row_bytes);
+    if (s != SKX_OK) return s;
+    if (N < 1 || F < 0 || F >= (int64_t(1) << 32) || !d_out || !d_rows) return SKX_EINVAL;
+    if (F > 0 && (!d_fk || (q->agg != SKX_AGG_COUNT && !d_measure))) return SKX_EINVAL;
+    if (!valid_stream_ptrs(d_fk) || !valid_stream_ptrs(d_measure) || !valid_stream_ptrs(d_rows) ||
+        (reinterpret_cast<uintptr_t>(d_out) & 7u))
+        return SKX_EINVAL;
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    ProbeArgs a{};
+    a.rows = d_rows;
+    a.N = N;
+    a.row_bytes = row_bytes;
+    a.fk = d_fk;
+    a.measure = d_measure;
+    a.F = F;
+    a.q = *q;
+    a.out = d_out;
+    a.err = err;
+    skx_tuning t{};
+    if (tuning) t = *tuning;
+    resolve_probe_tuning(a, t);
+    SKX_CUDA_TRY(launch_probe(a, t, static_cast<cudaStream_t>(stream)));
+    return SKX_OK;
+}
+
+skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_bytes, const int32_t *h_fk,
+                                   const int32_t *h_measure, int64_t F, const skx_query *q, int64_t *h_out,
+                                   void *stream) {
+    skx_status s = validate_query(q, row_bytes);
+    if (s != SKX_OK) return s;
+    if (N < 1 || F < 0 || F >= (int64_t(1) << 32) || !h_rows || !h_out) return SKX_EINVAL;
+    if (F > 0 && (!h_fk || (q->agg != SKX_AGG_COUNT && !h_measure))) return SKX_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nout = q->agg == SKX_AGG_GROUPBY_SUM ? q->num_groups : 1;
+    const size_t rows_b = size_t(N) * row_bytes, fk_b = size_t(F) * 4;
+    // clear any stale error bits so this call reports only its own
+    skx_status pre = skx_stream_status(stream);
+    if (pre == SKX_ECUDA || pre == SKX_ENOMEM) return pre;
+
+    char *d_rows = nullptr, *d_rows2 = nullptr;
+    int32_t *d_fk = nullptr, *d_m = nullptr;
+    int64_t *d_out = nullptr;
+    skx_index *idx = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows), rows_b, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows2), rows_b, st);
+    if (e == cudaSuccess && F > 0) e = cudaMallocAsync(reinterpret_cast<void **>(&d_fk), fk_b, st);
+    if (e == cudaSuccess && F > 0 && q->agg != SKX_AGG_COUNT) e = cudaMallocAsync(reinterpret_cast<void **>(&d_m), fk_b, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_out), size_t(nout) * 8, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rows, h_rows, rows_b, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && d_fk) e = cudaMemcpyAsync(d_fk, h_fk, fk_b, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && d_m) e = cudaMemcpyAsync(d_m, h_measure, fk_b, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) s = cuda_status(e);
+    if (s == SKX_OK) s = skx_build_index(d_fk, F, N, stream, &idx);
+    if (s == SKX_OK) s = skx_remap(idx, d_fk, d_fk, F, stream);
+    if (s == SKX_OK) s = skx_reorder(idx, d_rows, d_rows2, N, row_bytes, stream);
+    if (s == SKX_OK) s = skx_probe_aggregate(d_rows2, N, row_bytes, d_fk, d_m, F, q, d_out, nullptr, stream);
+    if (s == SKX_OK) {
+        e = cudaMemcpyAsync(h_out, d_out, size_t(nout) * 8, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) s = cuda_status(e);
+    }
+    skx_index_destroy(idx);
+    if (d_rows) cudaFreeAsync(d_rows, st);
+    if (d_rows2) cudaFreeAsync(d_rows2, st);
+    if (d_fk) cudaFreeAsync(d_fk, st);
+    if (d_m) cudaFreeAsync(d_m, st);
+    if (d_out) cudaFreeAsync(d_out, st);
+    skx_status fin = skx_stream_status(stream);
+    return s != SKX_OK ? s : fin;
+}
+
+}  // extern "C"

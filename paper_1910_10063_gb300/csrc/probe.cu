@@ -1,0 +1,345 @@
+// probe.cu -- FK-join probe + filter + aggregation over the (re)ordered
+// layout: the Q1 gather of a dimension row through the FK used as an array
+// offset, the Q2 predicate on one of its attributes, and a COUNT / SUM /
+// GROUP BY SUM aggregation (Sections I and IV-A of the paper).
+//
+// GB300 design.
+//  * Persistent grid (a multiple of the SM count); each thread streams the
+//    fk and measure columns with 16-byte loads marked L2 evict-first and keeps
+//    4 x UNROLL rows in flight, issuing all of their dimension gathers before
+//    consuming any of them.  Gathers carry an L2 evict-last policy so the
+//    popular dimension lines survive the fact stream.
+//  * Threshold-based processing (Section IV-B): after remapping, a key k < t
+//    is one of the t most popular rows.  Those rows are not gathered at all
+//    while streaming: the CTA adds the row's measure (or 1 for COUNT) into a
+//    per-key shared-memory sum, and at the end looks up each hot row once and
+//    folds sum * payload into its group.  This is exact in modular integer
+//    arithmetic: sum_i m_i * p == p * sum_i m_i (mod 2^64).
+//  * The t_lane hottest keys get one shared-memory copy per warp lane, so
+//    the lanes of a warp never collide on the same address -- the paper's
+//    per-SIMD-lane copies of the top values (Section IV-B, aggregation).
+//  * Group sums live in shared memory (int64, one per group) and are merged
+//    into the output with one global atomic per group per CTA: the paper's
+//    hybrid of private buffers for hot data and shared atomics (Section IV-C).
+//    COUNT and SUM accumulate in registers and reduce once per CTA.
+// With t = 0 the same kernel is the plain probe used on the original layout.
+#include "skx_internal.cuh"
+
+namespace skx {
+namespace {
+
+constexpr int kMaxSmemGroups = 4096;
+
+struct PP {
+    const int32_t *fk, *measure;
+    int64_t F, head;
+    const char *rows;
+    int32_t N, row_bytes;
+    int32_t fcol, flt, gcol, G, pcol;
+    int32_t t_hot, t_lane;
+    unsigned long long *out;
+    unsigned *err;
+};
+
+__device__ __forceinline__ int sel4(const int4 &v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+// Gathered values of one dimension row: x = filter column, y = group column, z = payload.
+template <bool FAST16, int AGG>
+__device__ __forceinline__ int4 fetch_row(const PP &p, int32_t k, uint64_t pol) {
+    const char *r = p.rows + size_t(k) * size_t(p.row_bytes);
+    int4 v;
+    if (FAST16) {
+        const int4 raw = ld_gather16(reinterpret_cast<const int4 *>(r), pol);
+        v.x = p.fcol >= 0 ? sel4(raw, p.fcol) : 0;
+        v.y = AGG == SKX_AGG_GROUPBY_SUM ? sel4(raw, p.gcol) : 0;
+        v.z = p.pcol >= 0 ? sel4(raw, p.pcol) : 1;
+    } else {
+        const int *ri = reinterpret_cast<const int *>(r);
+        v.x = p.fcol >= 0 ? ld_gather4(ri + p.fcol, pol) : 0;
+        v.y = AGG == SKX_AGG_GROUPBY_SUM ? ld_gather4(ri + p.gcol, pol) : 0;
+        v.z = (AGG != SKX_AGG_COUNT && p.pcol >= 0) ? ld_gather4(ri + p.pcol, pol) : 1;
+    }
+    v.w = 0;
+    return v;
+}
+
+__device__ __forceinline__ bool passes(const PP &p, const int4 &v) { return p.fcol < 0 || v.x < p.flt; }
+
+// Fold `amount` (a measure, a hot-key measure sum, or a count) for a row whose
+// gathered values are v.
+template <int AGG, bool GSMEM>
+__device__ __forceinline__ void fold(const PP &p, const int4 &v, unsigned long long amount, unsigned long long &acc,
+                                     unsigned long long *s_grp) {
+    if (!passes(p, v)) return;
+    if (AGG == SKX_AGG_COUNT) {
+        acc += amount;
+        return;
+    }
+    const unsigned long long prod = amount * (unsigned long long)(long long)v.z;
+    if (AGG == SKX_AGG_SUM) {
+        acc += prod;
+        return;
+    }
+    if ((uint32_t)v.y < (uint32_t)p.G) {
+        if (GSMEM)
+            atomicAdd(s_grp + v.y, prod);
+        else
+            atomicAdd(p.out + v.y, prod);
+    } else {
+        raise_error(p.err, kErrGroupRange);
+    }
+}
+
+template <int AGG, bool FAST16, bool GSMEM>
+__device__ __forceinline__ void handle(const PP &p, int32_t k, int32_t m, const int4 &row, unsigned long long &acc,
+                                       unsigned long long *s_grp, unsigned long long *s_hot,
+                                       unsigned long long *s_lane, unsigned lane) {
+    const unsigned long long amount = AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)m;
+    if ((uint32_t)k < (uint32_t)p.t_hot) {
+        if ((uint32_t)k < (uint32_t)p.t_lane)
+            atomicAdd(s_lane + (size_t(k) << 5) + lane, amount);
+        else
+            atomicAdd(s_hot + k, amount);
+    } else if ((uint32_t)k < (uint32_t)p.N) {
+        fold<AGG, GSMEM>(p, row, amount, acc, s_grp);
+    } else {
+        raise_error(p.err, kErrKeyRange);
+    }
+}
+
+template <int AGG, bool FAST16, bool GSMEM, int UNROLL>
+__global__ void __launch_bounds__(512) k_probe(PP p) {
+    extern __shared__ unsigned long long smem[];
+    const int ngrp = GSMEM ? p.G : 0;
+    unsigned long long *s_grp = smem;
+    unsigned long long *s_hot = smem + ngrp;
+    unsigned long long *s_lane = s_hot + p.t_hot;
+    const int nsm = ngrp + p.t_hot + (p.t_lane << 5);
+    for (int i = threadIdx.x; i < nsm; i += blockDim.x) smem[i] = 0;
+    __syncthreads();
+
+    const uint64_t pol_s = policy_evict_first();
+    const uint64_t pol_g = policy_evict_last();
+    const unsigned lane = lane_id();
+    unsigned long long acc = 0;
+
+    const int4 *fk4 = reinterpret_cast<const int4 *>(p.fk + p.head);
+    const int4 *m4 = reinterpret_cast<const int4 *>((AGG == SKX_AGG_COUNT ? p.fk : p.measure) + p.head);
+    const int64_t nvec = (p.F - p.head) >> 2;
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+
+    if (UNROLL > 0) {
+        constexpr int U = UNROLL > 0 ? UNROLL : 1;
+        for (int64_t base = tid; base < nvec; base += nthr * U) {
+            int32_t key[4 * U], mea[4 * U];
+            bool valid[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = base + u * nthr;
+                valid[u] = i < nvec;
+                int4 kv = make_int4(0, 0, 0, 0), mv = make_int4(0, 0, 0, 0);
+                if (valid[u]) {
+                    kv = ld_stream16(fk4 + i, pol_s);
+                    if (AGG != SKX_AGG_COUNT) mv = ld_stream16(m4 + i, pol_s);
+                }
+                key[4 * u + 0] = kv.x; key[4 * u + 1] = kv.y; key[4 * u + 2] = kv.z; key[4 * u + 3] = kv.w;
+                mea[4 * u + 0] = mv.x; mea[4 * u + 1] = mv.y; mea[4 * u + 2] = mv.z; mea[4 * u + 3] = mv.w;
+            }
+            int4 row[4 * U];
+#pragma unroll
+            for (int j = 0; j < 4 * U; ++j) {
+                const uint32_t k = (uint32_t)key[j];
+                row[j] = make_int4(0, 0, 0, 0);
+                if (valid[j / 4] && k >= (uint32_t)p.t_hot && k < (uint32_t)p.N)
+                    row[j] = fetch_row<FAST16, AGG>(p, key[j], pol_g);
+            }
+#pragma unroll
+            for (int j = 0; j < 4 * U; ++j)
+                if (valid[j / 4]) handle<AGG, FAST16, GSMEM>(p, key[j], mea[j], row[j], acc, s_grp, s_hot, s_lane, lane);
+        }
+        // unaligned head (< 4 rows) and ragged tail (< 4 rows)
+        if (tid < 8) {
+            const int64_t tail0 = p.head + (nvec << 2);
+            int64_t idx = -1;
+            if (tid < p.head) idx = tid;
+            else if (tid >= 4 && tail0 + (tid - 4) < p.F) idx = tail0 + (tid - 4);
+            if (idx >= 0) {
+                const int32_t k = p.fk[idx];
+                const int32_t m = AGG == SKX_AGG_COUNT ? 0 : p.measure[idx];
+                int4 row = make_int4(0, 0, 0, 0);
+                if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N)
+                    row = fetch_row<FAST16, AGG>(p, k, pol_g);
+                handle<AGG, FAST16, GSMEM>(p, k, m, row, acc, s_grp, s_hot, s_lane, lane);
+            }
+        }
+    } else {
+        // fk and measure at different offsets mod 16 bytes: 4-byte loads, one row per step
+        for (int64_t i = tid; i < p.F; i += nthr) {
+            const int32_t k = ld_stream4(p.fk + i, pol_s);
+            const int32_t m = AGG == SKX_AGG_COUNT ? 0 : ld_stream4(p.measure + i, pol_s);
+            int4 row = make_int4(0, 0, 0, 0);
+            if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N) row = fetch_row<FAST16, AGG>(p, k, pol_g);
+            handle<AGG, FAST16, GSMEM>(p, k, m, row, acc, s_grp, s_hot, s_lane, lane);
+        }
+    }
+    __syncthreads();
+
+    // hot prefix: one lookup per hot row per CTA
+    for (int k = threadIdx.x; k < p.t_hot; k += blockDim.x) {
+        unsigned long long s = s_hot[k];
+        if (k < p.t_lane) {
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) s += s_lane[(size_t(k) << 5) + l];
+        }
+        if (s == 0) continue;
+        const int4 v = fetch_row<FAST16, AGG>(p, k, pol_g);
+        fold<AGG, GSMEM>(p, v, s, acc, s_grp);
+    }
+
+    if (AGG == SKX_AGG_GROUPBY_SUM) {
+        if (GSMEM) {
+            __syncthreads();
+            for (int g = threadIdx.x; g < p.G; g += blockDim.x)
+                if (s_grp[g]) atomicAdd(p.out + g, s_grp[g]);
+        }
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0 && acc) atomicAdd(p.out, acc);
+    }
+}
+
+template <int AGG, bool FAST16, bool GSMEM, int UNROLL>
+cudaError_t launch_one(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st) {
+    auto kern = k_probe<AGG, FAST16, GSMEM, UNROLL>;
+    static int configured_smem = -1;  // per instantiation; the device limit is the same for all GB300s
+    const int want = device_max_smem_optin();
+    if (configured_smem != want) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e != cudaSuccess) return e;
+        configured_smem = want;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t.block_threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (t.ctas_per_sm > 0 && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;
+    const int sms = device_sm_count();
+    const int64_t work = UNROLL > 0 ? ((p.F - p.head) >> 2) : p.F;
+    const int64_t per_thread = UNROLL > 0 ? UNROLL : 1;
+    int64_t need = (work + int64_t(t.block_threads) * per_thread - 1) / (int64_t(t.block_threads) * per_thread);
+    int64_t grid = int64_t(sms) * per_sm;
+    if (need < grid) grid = need < 1 ? 1 : need;
+    kern<<<(unsigned)grid, t.block_threads, smem, st>>>(p);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <int AGG, bool FAST16, bool GSMEM>
+cudaError_t launch_unroll(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st, bool vec) {
+    if (!vec) return launch_one<AGG, FAST16, GSMEM, 0>(p, t, smem, st);
+    switch (t.unroll) {
+        case 1: return launch_one<AGG, FAST16, GSMEM, 1>(p, t, smem, st);
+        case 4: return launch_one<AGG, FAST16, GSMEM, 4>(p, t, smem, st);
+        default: return launch_one<AGG, FAST16, GSMEM, 2>(p, t, smem, st);
+    }
+}
+
+template <int AGG>
+cudaError_t launch_agg(const PP &p, bool fast16, bool gsmem, const skx_tuning &t, size_t smem, cudaStream_t st,
+                       bool vec) {
+    if (fast16) {
+        if (gsmem) return launch_unroll<AGG, true, true>(p, t, smem, st, vec);
+        return launch_unroll<AGG, true, false>(p, t, smem, st, vec);
+    }
+    if (gsmem) return launch_unroll<AGG, false, true>(p, t, smem, st, vec);
+    return launch_unroll<AGG, false, false>(p, t, smem, st, vec);
+}
+
+int32_t clamp32(int64_t v, int64_t lo, int64_t hi) { return (int32_t)(v < lo ? lo : (v > hi ? hi : v)); }
+
+}  // namespace
+
+skx_status validate_query(const skx_query *q, int32_t row_bytes) {
+    if (!q || row_bytes <= 0 || row_bytes % 4 != 0) return SKX_EINVAL;
+    const int32_t words = row_bytes / 4;
+    if (q->agg < SKX_AGG_COUNT || q->agg > SKX_AGG_GROUPBY_SUM) return SKX_EINVAL;
+    if (q->filter_col < -1 || q->filter_col >= words) return SKX_EINVAL;
+    if (q->payload_col < -1 || q->payload_col >= words) return SKX_EINVAL;
+    if (q->agg == SKX_AGG_GROUPBY_SUM) {
+        if (q->group_col < 0 || q->group_col >= words) return SKX_EINVAL;
+        if (q->num_groups < 1 || q->num_groups > (1 << 24)) return SKX_EINVAL;
+    }
+    return SKX_OK;
+}
+
+void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t) {
+    if (t.block_threads != 128 && t.block_threads != 256 && t.block_threads != 512)
+        t.block_threads = 512;
+    if (t.unroll != 1 && t.unroll != 2 && t.unroll != 4) t.unroll = 2;
+    const bool grp = a.q.agg == SKX_AGG_GROUPBY_SUM;
+    const int64_t gbytes = (grp && a.q.num_groups <= kMaxSmemGroups) ? int64_t(a.q.num_groups) * 8 : 0;
+    // lane copies
+    if (t.lane_keys < 0) t.lane_keys = 0;
+    else if (t.lane_keys == 0) t.lane_keys = 32;
+    // hot prefix sized so that two CTAs fit per SM by default
+    const int64_t budget = (int64_t)device_max_smem_optin() / 2 - 2048;
+    if (t.hot_keys < 0) {
+        t.hot_keys = 0;
+        t.lane_keys = 0;
+    } else {
+        if (t.hot_keys == 0) t.hot_keys = (int32_t)(((budget - gbytes - int64_t(t.lane_keys) * 256) / 8) & ~int64_t(1023));
+        const int64_t room = ((int64_t)device_max_smem_optin() - 1024 - gbytes) / 8;
+        t.hot_keys = clamp32(t.hot_keys, 0, a.N);
+        t.lane_keys = clamp32(t.lane_keys, 0, t.hot_keys);
+        if (int64_t(t.hot_keys) + int64_t(t.lane_keys) * 32 > room) {
+            t.lane_keys = clamp32(t.lane_keys, 0, room / 64);
+            t.hot_keys = clamp32(t.hot_keys, 0, room - int64_t(t.lane_keys) * 32);
+            t.lane_keys = clamp32(t.lane_keys, 0, t.hot_keys);
+        }
+    }
+    if (t.ctas_per_sm < 0) t.ctas_per_sm = 0;
+}
+
+cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t st) {
+    PP p{};
+    p.fk = a.fk;
+    p.measure = a.measure;
+    p.F = a.F;
+    p.rows = static_cast<const char *>(a.rows);
+    p.N = a.N;
+    p.row_bytes = a.row_bytes;
+    p.fcol = a.q.filter_col;
+    p.flt = a.q.filter_lt;
+    p.gcol = a.q.group_col;
+    p.G = a.q.agg == SKX_AGG_GROUPBY_SUM ? a.q.num_groups : 1;
+    p.pcol = a.q.payload_col;
+    p.t_hot = t.hot_keys;
+    p.t_lane = t.lane_keys;
+    p.out = reinterpret_cast<unsigned long long *>(a.out);
+    p.err = a.err;
+    const int nout = a.q.agg == SKX_AGG_GROUPBY_SUM ? a.q.num_groups : 1;
+    cudaError_t e = cudaMemsetAsync(a.out, 0, size_t(nout) * 8, st);
+    if (e != cudaSuccess || a.F <= 0) return e;
+
+    // vector path needs fk and measure at the same offset mod 16 bytes
+    const uintptr_t af = reinterpret_cast<uintptr_t>(a.fk) & 15u;
+    const uintptr_t am = a.q.agg == SKX_AGG_COUNT ? af : (reinterpret_cast<uintptr_t>(a.measure) & 15u);
+    const int64_t mis = (int64_t)(af >> 2);
+    p.head = mis ? (a.F < 4 - mis ? a.F : 4 - mis) : 0;
+    const bool fast16 = a.row_bytes % 16 == 0 && aligned16(a.rows) && p.fcol < 4 && p.gcol < 4 && p.pcol < 4;
+    const bool gsmem = a.q.agg == SKX_AGG_GROUPBY_SUM && a.q.num_groups <= kMaxSmemGroups;
+    const size_t smem = size_t((gsmem ? a.q.num_groups : 0) + t.hot_keys + t.lane_keys * 32) * 8;
+
+    const bool vec = af == am;
+    switch (a.q.agg) {
+        case SKX_AGG_COUNT: return launch_agg<SKX_AGG_COUNT>(p, fast16, gsmem, t, smem, st, vec);
+        case SKX_AGG_SUM: return launch_agg<SKX_AGG_SUM>(p, fast16, gsmem, t, smem, st, vec);
+        default: return launch_agg<SKX_AGG_GROUPBY_SUM>(p, fast16, gsmem, t, smem, st, vec);
+    }
+}
+
+}  // namespace skx

@@ -1,0 +1,134 @@
+// remap.cu -- apply the permutation index to both sides of the join.
+//
+//   remap    fk_out[i] = rank[fk_in[i]]        recode of column C into C'
+//                                              (Section III-A)
+//   reorder  rows_out[r] = rows_in[perm[r]]    permuted copy of the dimension
+//                                              rows (Section III-B)
+//
+// GB300 design: remap streams the fact column with 16-byte loads and stores
+// marked L2 evict-first, so that rank[] (4 B per id) stays L2-resident for
+// the random gathers; under skew most gathers hit a few hot lines.  Reorder
+// gives every 16-byte chunk of the output its own lane, so stores are fully
+// coalesced and each source row is read as one contiguous run.
+#include "skx_internal.cuh"
+
+namespace skx {
+namespace {
+
+constexpr int kRemapBlock = 512;
+constexpr int kRemapUnroll = 2;
+
+__device__ __forceinline__ int32_t remap_one(int32_t k, const int32_t *__restrict__ rank, int32_t N, unsigned *err) {
+    if ((uint32_t)k < (uint32_t)N) return __ldg(rank + k);
+    raise_error(err, kErrKeyRange);
+    return k;
+}
+
+template <bool INPLACE>
+__global__ void __launch_bounds__(kRemapBlock)
+    k_remap(const int32_t *__restrict__ rank, int32_t N, const int32_t *in, int32_t *out, int64_t F, int64_t head,
+            unsigned *err) {
+    const uint64_t pol = policy_evict_first();
+    const int4 *vin = reinterpret_cast<const int4 *>(in + head);
+    int4 *vout = reinterpret_cast<int4 *>(out + head);
+    const int64_t nvec = (F - head) >> 2;
+    const int64_t tid = int64_t(blockIdx.x) * kRemapBlock + threadIdx.x;
+    const int64_t nthr = int64_t(gridDim.x) * kRemapBlock;
+    for (int64_t base = tid; base < nvec; base += nthr * kRemapUnroll) {
+        int4 k[kRemapUnroll];
+#pragma unroll
+        for (int u = 0; u < kRemapUnroll; ++u) {
+            const int64_t i = base + u * nthr;
+            // in == out is allowed: each vector is read before it is written by the same thread
+            if (i < nvec) k[u] = INPLACE ? ld_stream16_rw(vin + i, pol) : ld_stream16(vin + i, pol);
+        }
+#pragma unroll
+        for (int u = 0; u < kRemapUnroll; ++u) {
+            const int64_t i = base + u * nthr;
+            if (i < nvec) {
+                int4 r;
+                r.x = remap_one(k[u].x, rank, N, err);
+                r.y = remap_one(k[u].y, rank, N, err);
+                r.z = remap_one(k[u].z, rank, N, err);
+                r.w = remap_one(k[u].w, rank, N, err);
+                st_stream16(vout + i, r, pol);
+            }
+        }
+    }
+    if (tid < 8) {  // unaligned head (< 4) and ragged tail (< 4)
+        const int64_t tail0 = head + (nvec << 2);
+        int64_t idx = -1;
+        if (tid < head) idx = tid;
+        else if (tid >= 4 && tail0 + (tid - 4) < F) idx = tail0 + (tid - 4);
+        if (idx >= 0) out[idx] = remap_one(in[idx], rank, N, err);
+    }
+}
+
+// Unaligned in/out pair (different offsets mod 16 bytes): plain 4-byte path.
+__global__ void __launch_bounds__(kRemapBlock)
+    k_remap_scalar(const int32_t *__restrict__ rank, int32_t N, const int32_t *in, int32_t *out, int64_t F,
+                   unsigned *err) {
+    for (int64_t i = int64_t(blockIdx.x) * kRemapBlock + threadIdx.x; i < F; i += int64_t(gridDim.x) * kRemapBlock)
+        out[i] = remap_one(in[i], rank, N, err);
+}
+
+template <typename Chunk>
+__global__ void __launch_bounds__(512)
+    k_reorder(const int32_t *__restrict__ perm, int32_t N, const Chunk *__restrict__ in, Chunk *__restrict__ out,
+              int32_t chunks_per_row) {
+    const int64_t total = int64_t(N) * chunks_per_row;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < total; j += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = j / chunks_per_row;
+        const int64_t c = j - r * chunks_per_row;
+        const int32_t src = __ldg(perm + r);
+        if ((uint32_t)src < (uint32_t)N) out[j] = in[int64_t(src) * chunks_per_row + c];
+    }
+}
+
+int grid_for(int64_t work_items, int block, int per_sm) {
+    const int sms = device_sm_count();
+    int64_t want = (work_items + block - 1) / block;
+    int64_t cap = (int64_t)sms * per_sm;
+    return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+}  // namespace
+
+cudaError_t launch_remap(const int32_t *d_rank, int32_t N, const int32_t *d_in, int32_t *d_out, int64_t F,
+                         unsigned *d_err, cudaStream_t st) {
+    if (F <= 0) return cudaSuccess;
+    const uintptr_t ai = reinterpret_cast<uintptr_t>(d_in) & 15u, ao = reinterpret_cast<uintptr_t>(d_out) & 15u;
+    if (ai != ao) {
+        k_remap_scalar<<<grid_for(F, kRemapBlock, 4), kRemapBlock, 0, st>>>(d_rank, N, d_in, d_out, F, d_err);
+        note_launches(1);
+        return cudaGetLastError();
+    }
+    const int64_t mis = (int64_t)(ai >> 2);
+    const int64_t head = mis ? (F < 4 - mis ? F : 4 - mis) : 0;
+    const int64_t nvec = (F - head) >> 2;
+    int grid = grid_for((nvec + kRemapUnroll - 1) / kRemapUnroll, kRemapBlock, 2048 / kRemapBlock);
+    if (d_in == d_out)
+        k_remap<true><<<grid, kRemapBlock, 0, st>>>(d_rank, N, d_in, d_out, F, head, d_err);
+    else
+        k_remap<false><<<grid, kRemapBlock, 0, st>>>(d_rank, N, d_in, d_out, F, head, d_err);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder(const int32_t *d_perm, int32_t N, const void *d_in, void *d_out, int32_t row_bytes,
+                           cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    if (row_bytes % 16 == 0 && aligned16(d_in) && aligned16(d_out)) {
+        const int32_t w = row_bytes / 16;
+        k_reorder<int4><<<grid_for(int64_t(N) * w, 512, 4), 512, 0, st>>>(
+            d_perm, N, static_cast<const int4 *>(d_in), static_cast<int4 *>(d_out), w);
+    } else {
+        const int32_t w = row_bytes / 4;
+        k_reorder<int32_t><<<grid_for(int64_t(N) * w, 512, 4), 512, 0, st>>>(
+            d_perm, N, static_cast<const int32_t *>(d_in), static_cast<int32_t *>(d_out), w);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace skx

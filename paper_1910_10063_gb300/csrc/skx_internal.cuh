@@ -1,0 +1,136 @@
+// skx_internal.cuh -- shared definitions of the CUDA translation units of libskx.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/skx.h"
+
+namespace skx {
+
+// bits of the per-device data-error word
+constexpr unsigned kErrKeyRange = 1u;
+constexpr unsigned kErrGroupRange = 2u;
+constexpr unsigned kErrTimeout = 4u;
+
+constexpr int kWarp = 32;
+
+// -------------------------------------------------------------- host helpers
+skx_status cuda_status(cudaError_t e);          // records the message, maps to SKX_ECUDA
+unsigned *device_error_word();                  // per-device word (lazily allocated)
+int device_sm_count();                          // SMs of the current device
+int device_max_smem_optin();                    // max dynamic smem per block (opt-in)
+void note_launches(int n);                      // adds to the process-wide kernel-launch counter
+
+#define SKX_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) return ::skx::cuda_status(e__); \
+    } while (0)
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// -------------------------------------------------------------- device helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// L2 eviction-priority policies (createpolicy) for loads that stream through
+// once (evict_first) and for gathers whose lines should outlive the stream
+// (evict_last).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 16-byte streaming load: read-only path, no L1 allocation, L2 evict-first.
+__device__ __forceinline__ int4 ld_stream16(const int4 *p, uint64_t pol) {
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+// Same through the coherent path, for data the kernel itself overwrites (in-place remap).
+__device__ __forceinline__ int4 ld_stream16_rw(const int4 *p, uint64_t pol) {
+    int4 v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int ld_stream4(const int *p, uint64_t pol) {
+    int v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+                 : "=r"(v)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+// 16-byte streaming store (evict-first in L2).
+__device__ __forceinline__ void st_stream16(int4 *p, int4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.s32 [%0], {%1,%2,%3,%4}, %5;"
+                 :
+                 : "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+// gathers through the read-only path with an explicit L2 policy
+__device__ __forceinline__ int4 ld_gather16(const int4 *p, uint64_t pol) {
+    int4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int ld_gather4(const int *p, uint64_t pol) {
+    int v;
+    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void raise_error(unsigned *err, unsigned bit) {
+    if (err) atomicOr(err, bit);
+}
+
+// -------------------------------------------------------------- internal entry points
+// (launchers shared between the C-ABI implementation and the batch/serving paths)
+
+// Histogram of keys[F] into cnt[N] (cnt must be zeroed by the caller).
+cudaError_t launch_histogram(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_cnt, unsigned *d_err,
+                             cudaStream_t st);
+
+// Scratch bytes the frequency sort needs for N ids and F rows.
+size_t sort_scratch_bytes(int32_t N, int64_t F);
+// Sorts ids by (cnt desc, id asc): writes perm (new->old) and rank (old->new).
+cudaError_t launch_sort_by_count(const uint32_t *d_cnt, int32_t N, int64_t F, int32_t *d_perm, int32_t *d_rank,
+                                 void *d_scratch, size_t scratch_bytes, cudaStream_t st);
+
+cudaError_t launch_remap(const int32_t *d_rank, int32_t N, const int32_t *d_in, int32_t *d_out, int64_t F,
+                         unsigned *d_err, cudaStream_t st);
+cudaError_t launch_reorder(const int32_t *d_perm, int32_t N, const void *d_in, void *d_out, int32_t row_bytes,
+                           cudaStream_t st);
+
+struct ProbeArgs {
+    const void *rows;
+    int32_t N, row_bytes;
+    const int32_t *fk, *measure;
+    int64_t F;
+    skx_query q;
+    int64_t *out;
+    unsigned *err;
+};
+// Resolves defaults in `t` (in place) for these arguments.
+void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t);
+cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t st);
+skx_status validate_query(const skx_query *q, int32_t row_bytes);
+
+}  // namespace skx

@@ -215,3 +215,95 @@ def lognormal_sizes(count: int, seed: int, median: float = 2e5, sigma: float = 1
     g = np.random.Generator(np.random.PCG64(stream_key(seed, 6)))
     z = g.standard_normal(count)
     return np.clip(np.round(median * np.exp(sigma * z)), lo, hi).astype(np.int64)
+
+
+# ---------------------------------------------------------------- device twin
+_dev_lib = None
+
+
+def _synth_lib():
+    """libskx_synth.so (the CUDA twin of the functions above)."""
+    global _dev_lib
+    if _dev_lib is None:
+        import ctypes
+        import os
+        path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "libskx_synth.so")
+        if not os.path.exists(path):
+            raise RuntimeError(f"libskx_synth.so is not built at {path}; run `python -m paper_1910_10063_gb300.build`")
+        L = ctypes.CDLL(path)
+        P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        L.skx_synth_zipf.argtypes = [P, P, i32, u64, i64, i64, P, P]
+        L.skx_synth_uniform.argtypes = [u64, i64, i64, i32, ctypes.c_uint32, P, P]
+        L.skx_synth_rows.argtypes = [u64, i64, i32, P, P, P, P]
+        for f in ("skx_synth_zipf", "skx_synth_uniform", "skx_synth_rows"):
+            getattr(L, f).restype = ctypes.c_int
+        _dev_lib = L
+    return _dev_lib
+
+
+def _stream_ptr(stream):
+    import ctypes
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def zipf_fk_device(d_cdf, d_r2id, seed: int, count: int, start: int = 0, out=None, stream=None):
+    """int32 CUDA tensor of `count` Zipf FKs, elements start..start+count-1 of the stream."""
+    import ctypes
+    import torch
+    if out is None:
+        out = torch.empty(count, dtype=torch.int32, device=d_cdf.device)
+    st = _synth_lib().skx_synth_zipf(ctypes.c_void_p(d_cdf.data_ptr()), ctypes.c_void_p(d_r2id.data_ptr()),
+                                     d_cdf.numel(), stream_key(seed, STREAM_FK), start, count,
+                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    if st:
+        raise RuntimeError(f"skx_synth_zipf failed ({st})")
+    return out
+
+
+def measure_device(seed: int, count: int, start: int = 0, lo: int = 1, rng: int = 100, out=None, device="cuda",
+                   stream=None):
+    import ctypes
+    import torch
+    if out is None:
+        out = torch.empty(count, dtype=torch.int32, device=device)
+    st = _synth_lib().skx_synth_uniform(stream_key(seed, STREAM_MEASURE), start, count, lo, rng,
+                                        ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    if st:
+        raise RuntimeError(f"skx_synth_uniform failed ({st})")
+    return out
+
+
+def dim_rows_device(n: int, width: int, seed: int, num_groups: int = 1000, out=None, device="cuda", stream=None):
+    import ctypes
+    import torch
+    cols = dim_column_ranges(width, num_groups)
+    lo = np.array([c[0] for c in cols], dtype=np.int32)
+    rg = np.array([c[1] for c in cols], dtype=np.uint32)
+    if out is None:
+        out = torch.empty((n, width), dtype=torch.int32, device=device)
+    st = _synth_lib().skx_synth_rows(stream_key(seed, STREAM_DIM), n, width, lo.ctypes.data_as(ctypes.c_void_p),
+                                     rg.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(out.data_ptr()),
+                                     _stream_ptr(stream))
+    if st:
+        raise RuntimeError(f"skx_synth_rows failed ({st})")
+    return out
+
+
+class DeviceWorkload:
+    """A Workload generated on the device (same values as the host twin)."""
+
+    def __init__(self, n: int, f: int, s: float, seed: int = 0, width: int = 16, num_groups: int = 1000,
+                 r2id: np.ndarray | None = None, device="cuda", with_measure: bool = True,
+                 with_dim: bool = True):
+        import torch
+        self.n, self.f, self.s, self.seed, self.width = int(n), int(f), float(s), int(seed), int(width)
+        self.num_groups = num_groups
+        self.r2id_host = rank_to_id(self.n, self.seed) if r2id is None else r2id
+        cdf = zipf_cdf(self.n, self.s)
+        self.cdf = torch.from_numpy(cdf).to(device)
+        self.r2id = torch.from_numpy(self.r2id_host).to(device)
+        self.fk = zipf_fk_device(self.cdf, self.r2id, self.seed, self.f)
+        self.measure = measure_device(self.seed, self.f, device=device) if with_measure else None
+        self.dim = dim_rows_device(self.n, self.width, self.seed, num_groups, device=device) if with_dim else None

@@ -1,0 +1,334 @@
+"""Parity of every CUDA step with the CPU oracle, element by element, through
+the C ABI (via the ctypes binding).  Integer work: the bar is bit-exact."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1910_10063_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # the -m gpu suite runs only where a GPU exists
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1910_10063_gb300 as skx  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def offset_view(a: np.ndarray, offset: int):
+    """Device copy of `a` starting `offset` int32 elements into a larger buffer
+    (exercises the unaligned head/tail paths)."""
+    buf = torch.zeros(a.size + offset + 8, dtype=torch.int32, device=DEV)
+    v = buf[offset:offset + a.size]
+    v.copy_(torch.from_numpy(np.ascontiguousarray(a).reshape(-1)))
+    return v
+
+
+def status():
+    return skx.skx_stream_status()
+
+
+# ------------------------------------------------------------------ generator
+def test_synth_device_matches_host():
+    for n, f, s in [(1, 10, 1.0), (1000, 12345, 0.0), (5000, 100_000, 1.0), (300, 50_001, 1.5)]:
+        w = synth.Workload(n, f, s, seed=3, width=16)
+        d = synth.DeviceWorkload(n, f, s, seed=3, width=16)
+        assert np.array_equal(d.fk.cpu().numpy(), w.fk())
+        assert np.array_equal(d.measure.cpu().numpy(), w.measure())
+        assert np.array_equal(d.dim.cpu().numpy(), w.dim())
+
+
+def test_synth_device_sampled_at_scale():
+    n, f = 2_000_000, 50_000_000
+    d = synth.DeviceWorkload(n, f, 1.0, seed=11, width=16)
+    idx = np.random.default_rng(0).integers(0, f, 20000)
+    cdf = synth.zipf_cdf(n, 1.0)
+    fk = d.fk.cpu().numpy()
+    assert np.array_equal(fk[idx], synth.zipf_fk_host_at(cdf, d.r2id_host, 11, idx))
+    assert np.array_equal(d.measure.cpu().numpy()[idx], synth.measure_host_at(11, idx))
+    rows = np.random.default_rng(1).integers(0, n, 5000)
+    assert np.array_equal(d.dim.cpu().numpy()[rows], synth.dim_rows_host_at(rows, 16, 11))
+
+
+# ------------------------------------------------------------------ build index
+CASES = [  # (N, F, s, seed)
+    (1, 0, 1.0, 0),
+    (1, 17, 1.0, 0),
+    (7, 1, 0.0, 1),
+    (100, 4099, 1.0, 2),        # ragged tail, > 1 tile of ids? (no: N small) several vectors
+    (4097, 100_003, 1.2, 3),    # two sort tiles with a ragged last tile
+    (50_000, 1_000_001, 1.0, 4),
+    (20_000, 300_000, 0.0, 5),  # uniform: many equal counts -> ties by id
+    (9000, 2_000_000, 1.5, 6),  # heavy skew, counts > 2^16 (3 radix passes)
+    (100_000, 1_000_000, 1.0, 0),  # the 100K x 1M case, seed 0
+]
+
+
+@pytest.mark.parametrize("n,f,s,seed", CASES)
+def test_build_index_parity(n, f, s, seed):
+    w = synth.Workload(n, f, s, seed=seed, width=4)
+    fk = w.fk()
+    idx = skx.skx_build_index(dev(fk), n)
+    cnt, perm, rank = oracle.build_index(fk, n)
+    assert status() == skx.SKX_OK
+    assert np.array_equal(idx.counts.cpu().numpy().view(np.uint32).astype(np.uint64), cnt)
+    assert np.array_equal(idx.perm.cpu().numpy(), perm)
+    assert np.array_equal(idx.rank.cpu().numpy(), rank)
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_build_index_unaligned(offset):
+    w = synth.Workload(3000, 77_777, 1.0, seed=9)
+    fk = w.fk()
+    idx = skx.skx_build_index(offset_view(fk, offset), 3000)
+    cnt, perm, rank = oracle.build_index(fk, 3000)
+    assert np.array_equal(idx.perm.cpu().numpy(), perm)
+    assert np.array_equal(idx.counts.cpu().numpy().view(np.uint32).astype(np.uint64), cnt)
+
+
+def test_build_index_all_same_key_and_ties():
+    n = 5000
+    fk = np.full(123_457, 4321, dtype=np.int32)
+    idx = skx.skx_build_index(dev(fk), n)
+    perm = idx.perm.cpu().numpy()
+    assert perm[0] == 4321
+    assert np.array_equal(perm[1:], np.delete(np.arange(n), 4321))  # the zero counts, ascending ids
+    fk = np.arange(n, dtype=np.int32)[::-1].copy()  # every count 1 -> identity
+    assert np.array_equal(skx.skx_build_index(dev(fk), n).perm.cpu().numpy(), np.arange(n))
+
+
+def test_fig2_worked_example_on_gpu():
+    from oracle_pins import load_fig2
+    g = load_fig2()
+    order = [int(x) - 1 for x in g["offset_order"]]
+    fk = np.concatenate([np.full(8 - r, v, dtype=np.int32) for r, v in enumerate(order)])
+    fk = fk[np.random.default_rng(7).permutation(fk.size)]
+    idx = skx.skx_build_index(dev(fk), 8)
+    assert idx.perm.cpu().numpy().tolist() == order
+    rows = dev(np.array([[ord(c)] * 4 for c in g["dimension_rows"]], dtype=np.int32))
+    out = torch.empty_like(rows)
+    skx.skx_reorder(idx, rows, out)
+    assert [chr(x) for x in out[:, 0].cpu().tolist()] == g["reordered_rows"]
+
+
+# ------------------------------------------------------------------ remap / reorder
+@pytest.mark.parametrize("n,f,s,seed", CASES[1:7])
+def test_remap_parity(n, f, s, seed):
+    w = synth.Workload(n, f, s, seed=seed)
+    fk = w.fk()
+    d_fk = dev(fk)
+    idx = skx.skx_build_index(d_fk, n)
+    _, perm, rank = oracle.build_index(fk, n)
+    want = oracle.remap(rank, fk)
+    out = torch.empty_like(d_fk)
+    skx.skx_remap(idx, d_fk, out)
+    assert np.array_equal(out.cpu().numpy(), want)
+    skx.skx_remap(idx, d_fk, d_fk)  # in place
+    assert np.array_equal(d_fk.cpu().numpy(), want)
+    for off_in, off_out in [(1, 1), (2, 3), (0, 1)]:
+        a = offset_view(fk, off_in)
+        b = offset_view(np.zeros_like(fk), off_out)
+        skx.skx_remap(idx, a, b)
+        assert np.array_equal(b.cpu().numpy(), want)
+    assert status() == skx.SKX_OK
+
+
+@pytest.mark.parametrize("width", [1, 3, 4, 16, 17])
+def test_reorder_parity(width):
+    n = 10_007
+    w = synth.Workload(n, 200_000, 1.0, seed=width, width=width)
+    fk, dim = w.fk(), w.dim()
+    idx = skx.skx_build_index(dev(fk), n)
+    _, perm, _ = oracle.build_index(fk, n)
+    d_in = dev(dim)
+    d_out = torch.empty_like(d_in)
+    skx.skx_reorder(idx, d_in, d_out)
+    assert np.array_equal(d_out.cpu().numpy(), oracle.reorder(perm, dim))
+
+
+def test_reorder_unaligned_rows():
+    n, width = 999, 4
+    w = synth.Workload(n, 20_000, 1.0, seed=2, width=width)
+    fk, dim = w.fk(), w.dim()
+    idx = skx.skx_build_index(dev(fk), n)
+    _, perm, _ = oracle.build_index(fk, n)
+    buf = torch.zeros(n * width + 1, dtype=torch.int32, device=DEV)
+    src = buf[1:].view(n, width)
+    src.copy_(dev(dim))
+    dst = torch.empty_like(src)
+    skx.skx_reorder(idx, src, dst)
+    assert np.array_equal(dst.cpu().numpy(), oracle.reorder(perm, dim))
+
+
+# ------------------------------------------------------------------ probe
+TUNINGS = {
+    "plain": lambda: skx.Tuning.plain(),
+    "default": lambda: None,
+    "hot64_lane8": lambda: _tuning(hot_keys=64, lane_keys=8),
+    "hot1_nolane": lambda: _tuning(hot_keys=1, lane_keys=-1),
+    "block128_u1": lambda: _tuning(block_threads=128, unroll=1),
+    "block256_u4": lambda: _tuning(block_threads=256, unroll=4, hot_keys=3000, lane_keys=32),
+}
+
+
+def _tuning(**kw):
+    t = skx.Tuning()
+    for k, v in kw.items():
+        setattr(t, k, v)
+    return t
+
+
+QUERIES = {
+    "groupby": dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=1, filter_lt=50, group_col=0, num_groups=1000, payload_col=2),
+    "sum": dict(agg=oracle.AGG_SUM, filter_col=1, filter_lt=50, group_col=0, num_groups=1, payload_col=2),
+    "count": dict(agg=oracle.AGG_COUNT, filter_col=1, filter_lt=50, group_col=0, num_groups=1, payload_col=-1),
+    "groupby_nofilter_payload1": dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=-1, filter_lt=0, group_col=0,
+                                      num_groups=1000, payload_col=-1),
+    "sum_payload3": dict(agg=oracle.AGG_SUM, filter_col=1, filter_lt=10, group_col=0, num_groups=1, payload_col=3),
+}
+
+
+def _q(d):
+    return skx.Query(d["agg"], d["filter_col"], d["filter_lt"], d["group_col"], d["num_groups"], d["payload_col"])
+
+
+def _oracle(rows, fk, m, d):
+    return oracle.probe(rows, fk, m, d["agg"], d["filter_col"], d["filter_lt"], d["group_col"], d["num_groups"],
+                        d["payload_col"], nthreads=8)
+
+
+@pytest.fixture(scope="module")
+def probe_data():
+    w = synth.Workload(60_000, 1_000_003, 1.2, seed=21, width=16)
+    fk, m, dim = w.fk(), w.measure(), w.dim()
+    cnt, perm, rank = oracle.build_index(fk, w.n)
+    fk2, dim2 = oracle.remap(rank, fk), oracle.reorder(perm, dim)
+    return dict(fk=fk, m=m, dim=dim, fk2=fk2, dim2=dim2, d_fk=dev(fk), d_m=dev(m), d_dim=dev(dim),
+                d_fk2=dev(fk2), d_dim2=dev(dim2))
+
+
+@pytest.mark.parametrize("qname", list(QUERIES))
+@pytest.mark.parametrize("tname", list(TUNINGS))
+def test_probe_parity(probe_data, qname, tname):
+    d = QUERIES[qname]
+    want = _oracle(probe_data["dim"], probe_data["fk"], probe_data["m"], d)
+    q = _q(d)
+    for rows, fk in [(probe_data["d_dim"], probe_data["d_fk"]), (probe_data["d_dim2"], probe_data["d_fk2"])]:
+        got = skx.skx_probe_aggregate(rows, fk, probe_data["d_m"], q, tuning=TUNINGS[tname]())
+        assert np.array_equal(got.cpu().numpy(), want), (qname, tname)
+    assert status() == skx.SKX_OK
+
+
+def test_probe_generic_columns_and_narrow_rows(probe_data):
+    # filter/group/payload outside the first 16 bytes -> per-column gathers
+    d = dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=5, filter_lt=0, group_col=0, num_groups=1000, payload_col=9)
+    want = _oracle(probe_data["dim"], probe_data["fk"], probe_data["m"], d)
+    got = skx.skx_probe_aggregate(probe_data["d_dim2"], probe_data["d_fk2"], probe_data["d_m"], _q(d))
+    assert np.array_equal(got.cpu().numpy(), want)
+    # 12-byte rows (not a multiple of 16)
+    dim3 = np.ascontiguousarray(probe_data["dim2"][:, :3])
+    d = QUERIES["groupby"]
+    want = _oracle(dim3, probe_data["fk2"], probe_data["m"], d)
+    got = skx.skx_probe_aggregate(dev(dim3), probe_data["d_fk2"], probe_data["d_m"], _q(d))
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_probe_many_groups_global_path():
+    n, f, G = 20_000, 300_001, 50_000
+    w = synth.Workload(n, f, 1.0, seed=5, width=4, num_groups=G)
+    fk, m, dim = w.fk(), w.measure(), w.dim()
+    d = dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=1, filter_lt=50, group_col=0, num_groups=G, payload_col=2)
+    want = _oracle(dim, fk, m, d)
+    for t in (skx.Tuning.plain(), None):
+        got = skx.skx_probe_aggregate(dev(dim), dev(fk), dev(m), _q(d), tuning=t)
+        assert np.array_equal(got.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("off_fk,off_m", [(1, 1), (3, 3), (1, 2), (0, 3)])
+def test_probe_unaligned(probe_data, off_fk, off_m):
+    d = QUERIES["groupby"]
+    fk, m = probe_data["fk2"][:200_001], probe_data["m"][:200_001]
+    want = _oracle(probe_data["dim2"], fk, m, d)
+    got = skx.skx_probe_aggregate(probe_data["d_dim2"], offset_view(fk, off_fk), offset_view(m, off_m), _q(d))
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("f", [0, 1, 2, 3, 5, 31, 4097])
+def test_probe_tiny_and_ragged(probe_data, f):
+    for qname in ("groupby", "count", "sum"):
+        d = QUERIES[qname]
+        want = _oracle(probe_data["dim2"], probe_data["fk2"][:f], probe_data["m"][:f], d)
+        got = skx.skx_probe_aggregate(probe_data["d_dim2"], probe_data["d_fk2"][:f].contiguous(),
+                                      probe_data["d_m"][:f].contiguous(), _q(d))
+        assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_probe_wraparound_and_negative():
+    big = 2**31 - 1
+    rows = np.array([[0, 0, big, 0], [1, 0, -big - 1, 0], [1, 0, -7, 0]], dtype=np.int32)
+    fk = np.array(([0] * 6 + [1] * 3 + [2] * 5) * 1000, dtype=np.int32)
+    m = np.array(([big] * 6 + [-big - 1] * 3 + [-3] * 5) * 1000, dtype=np.int32)
+    for d in (QUERIES["groupby"], QUERIES["sum"]):
+        d = dict(d, num_groups=2 if d["agg"] == oracle.AGG_GROUPBY_SUM else 1)
+        want = _oracle(rows, fk, m, d)
+        for t in (skx.Tuning.plain(), None, _tuning(hot_keys=1, lane_keys=1)):
+            got = skx.skx_probe_aggregate(dev(rows), dev(fk), dev(m), _q(d), tuning=t)
+            assert np.array_equal(got.cpu().numpy(), want)
+
+
+# ------------------------------------------------------------------ errors
+def test_key_and_group_range_errors():
+    status()  # clear
+    rows = dev(np.array([[0, 0, 1, 1], [5, 0, 1, 1]], dtype=np.int32))
+    m = dev(np.ones(8, dtype=np.int32))
+    q = skx.Query.groupby_sum(num_groups=3, filter_lt=10)
+    skx.skx_probe_aggregate(rows, dev(np.array([0, 0, 0, 0, 0, 0, 0, 2], dtype=np.int32)), m, q,
+                            tuning=skx.Tuning.plain())
+    assert status() == skx.SKX_EKEYRANGE
+    skx.skx_probe_aggregate(rows, dev(np.array([0, 1, 0, 0, 0, 0, 0, 0], dtype=np.int32)), m, q,
+                            tuning=skx.Tuning.plain())
+    assert status() == skx.SKX_EGROUPRANGE
+    skx.skx_build_index(dev(np.array([0, 1, 9], dtype=np.int32)), 3)
+    assert status() == skx.SKX_EKEYRANGE
+    assert status() == skx.SKX_OK  # cleared
+    with pytest.raises(skx.SkxError) as e:
+        skx.skx_probe_aggregate(rows, dev(np.zeros(4, dtype=np.int32)), m[:4].contiguous(),
+                                skx.Query.groupby_sum(num_groups=0))
+    assert e.value.status == skx.SKX_EINVAL
+    with pytest.raises(skx.SkxError):
+        skx.skx_build_index(dev(np.zeros(4, dtype=np.int32)), 0)
+
+
+# ------------------------------------------------------------------ whole path
+def test_small_config_end_to_end():
+    """N = 100K x 4 int32, F = 1M, Zipf s = 1.0, seed 0: build -> remap -> reorder -> probe."""
+    w = synth.Workload(100_000, 1_000_000, 1.0, seed=0, width=4)
+    fk, m, dim = w.fk(), w.measure(), w.dim()
+    d_fk = dev(fk)
+    idx = skx.skx_build_index(d_fk, w.n)
+    fk2 = torch.empty_like(d_fk)
+    skx.skx_remap(idx, d_fk, fk2)
+    dim2 = torch.empty((w.n, 4), dtype=torch.int32, device=DEV)
+    skx.skx_reorder(idx, dev(dim), dim2)
+    got = skx.skx_probe_aggregate(dim2, fk2, dev(m), skx.Query.groupby_sum())
+    plain = skx.skx_probe_aggregate(dev(dim), d_fk, dev(m), skx.Query.groupby_sum(), tuning=skx.Tuning.plain())
+    want = oracle.probe(dim, fk, m, nthreads=8)
+    assert np.array_equal(got.cpu().numpy(), want)
+    assert np.array_equal(plain.cpu().numpy(), want)
+    assert status() == skx.SKX_OK
+
+
+def test_join_aggregate_host_api():
+    w = synth.Workload(30_000, 400_001, 1.0, seed=8, width=16)
+    fk, m, dim = w.fk(), w.measure(), w.dim()
+    for qname in ("groupby", "sum", "count"):
+        d = QUERIES[qname]
+        got = skx.skx_join_aggregate_host(dim, fk, m, _q(d))
+        assert np.array_equal(got, _oracle(dim, fk, m, d))
