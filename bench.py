@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 512 << 20
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=20_000_000, help="dimension rows")
@@ -51,7 +51,7 @@ def parse_args():
     p.add_argument("--sweep-steps", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-rows", type=int, default=20_000_000, help="fact rows in the oracle's timed sample")
+    p.add_argument("--cpu-rows", type=int, default=0, help="fact rows in the oracle's timed sample (0 = all F)")
     p.add_argument("--ref-rows", type=int, default=4_000_000, help="fact rows per reference-arm step")
     return p.parse_args()
 
@@ -117,7 +117,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -180,6 +180,14 @@ def run_ours(a, rank, world, local_rank):
 
     stages = ["count", "sort", "remap", "reorder", "probe"]
 
+    # probe launch shape and hot-prefix size: chosen once by the library's autotuner on
+    # this data (setup, outside the timed region)
+    idx0 = skx.skx_build_index(w.fk, a.n)
+    skx.skx_remap(idx0, w.fk, fk2)
+    skx.skx_reorder(idx0, w.dim, dim2)
+    tuning, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True)
+    idx0.close()
+
     def step(ev):
         ev[0].record(stream)
         skx.skx_count(w.fk, a.n, counts)
@@ -190,7 +198,7 @@ def run_ours(a, rank, world, local_rank):
         ev[3].record(stream)
         skx.skx_reorder(idx, w.dim, dim2)
         ev[4].record(stream)
-        skx.skx_probe_aggregate(dim2, fk2, w.measure, q, out=out)
+        skx.skx_probe_aggregate(dim2, fk2, w.measure, q, out=out, tuning=tuning)
         ev[5].record(stream)
         return idx
 
@@ -265,9 +273,14 @@ def run_ours(a, rank, world, local_rank):
             idx = skx.skx_build_index(fk_s, a.n)
             skx.skx_remap(idx, fk_s, fk2)
             skx.skx_reorder(idx, w.dim, dim2)
-            variants = {"plain": (w.dim, fk_s, skx.Tuning.plain()),
-                        "remapped_no_hot_prefix": (dim2, fk2, skx.Tuning.plain()),
-                        "remapped": (dim2, fk2, None)}
+            # every variant gets the autotuner's best shape for its own data; only the
+            # remapped layout may use a hot prefix (its ids are frequency ranks)
+            t_plain, _ = skx.skx_probe_autotune(w.dim, fk_s, w.measure, q, remapped=False)
+            t_lay, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=False)
+            t_rem, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True)
+            variants = {"plain": (w.dim, fk_s, t_plain),
+                        "remapped_no_hot_prefix": (dim2, fk2, t_lay),
+                        "remapped": (dim2, fk2, t_rem)}
             res, times = {}, {}
             for name, (rows, keys, tun) in variants.items():
                 o = torch.empty(1000, dtype=torch.int64, device=dev)
@@ -292,8 +305,11 @@ def run_ours(a, rank, world, local_rank):
             for name, ms in times.items():
                 med = statistics.median(ms)
                 gbs = (8 * a.f + 16 * Ds) / (med * 1e-3) / 1e9
+                tun = variants[name][2]
                 entry[name] = {"ms": round(med, 4), "grows_s": round(a.f / (med * 1e-3) / 1e9, 2),
-                               "frac_hbm": round(gbs / peak, 4)}
+                               "frac_hbm": round(gbs / peak, 4),
+                               "tuning": {k: tun.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
+                                                                         "hot_keys", "lane_keys")}}
             entry["speedup_remapped_vs_plain"] = round(entry["plain"]["ms"] / entry["remapped"]["ms"], 3)
             entry["speedup_layout_only"] = round(entry["plain"]["ms"] / entry["remapped_no_hot_prefix"]["ms"], 3)
             sweep.append(entry)
@@ -341,7 +357,8 @@ def run_ours(a, rank, world, local_rank):
     # ---------------- CPU baseline: the oracle on a bounded sample
     cpu = None
     if not a.no_cpu and rank == 0 and world == 1:
-        cpu = cpu_baseline(a, fk_host=w.fk[:a.cpu_rows].cpu().numpy(), m_host=w.measure[:a.cpu_rows].cpu().numpy(),
+        rows = a.cpu_rows if 0 < a.cpu_rows < a.f else a.f
+        cpu = cpu_baseline(a, fk_host=w.fk[:rows].cpu().numpy(), m_host=w.measure[:rows].cpu().numpy(),
                            dim_host=w.dim.cpu().numpy())
 
     if rank != 0:
@@ -355,6 +372,8 @@ def run_ours(a, rank, world, local_rank):
         "step": "count -> sort by frequency -> remap fk -> reorder dimension -> probe (filter + GROUP BY SUM)",
         "region_s": round(region_s, 3), "gpu_launches": int(launches),
         "roofline": roofline, "stages": stage_rep,
+        "probe_tuning": {k: tuning.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll", "hot_keys",
+                                                          "lane_keys")},
         "probe": {"remapped_p50_ms": round(statistics.median(probe_lat), 4) if probe_lat else None,
                   "remapped_p99_ms": round(float(np.percentile(probe_lat, 99)), 4) if probe_lat else None,
                   "sweep": sweep},

@@ -168,15 +168,19 @@ typedef struct skx_query {
 } skx_query;
 
 /* Launch and threshold parameters; zero-initialise and set what you need.
- * A field left at 0 takes the library default (chosen from N, F and the
- * device); hot_keys = -1 disables the hot prefix (plain processing). */
+ * A field left at 0 takes the library default (chosen from N, F, the query
+ * and the device).  Resolved values never contain 0: "off" and "as many as
+ * fit" are -1. */
 typedef struct skx_tuning {
-    int32_t block_threads; /* 128, 256 or 512 */
-    int32_t ctas_per_sm;   /* resident CTAs per SM targeted by the persistent grid */
-    int32_t hot_keys;      /* t: keys [0, t) aggregated per key in shared memory; -1 = off */
-    int32_t lane_keys;     /* keys [0, t_lane) (t_lane <= t) get one copy per warp lane; -1 = off */
-    int32_t warp_aggregate;/* 1: merge equal group keys within a warp before the atomic; -1 = off */
-    int32_t unroll;        /* 16-byte vectors per thread per iteration: 1, 2 or 4 */
+    int32_t block_threads; /* 128, 256 or 512 (default 512) */
+    int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent grid; default 1024 threads
+                              per SM; -1 = as many as fit */
+    int32_t hot_keys;      /* t: keys [0, t) aggregated per key in shared memory (default: as
+                              many as fit with two CTAs per SM); -1 = off (plain processing) */
+    int32_t lane_keys;     /* keys [0, t_lane), t_lane <= t, get one copy per warp lane
+                              (default 32); -1 = off */
+    int32_t warp_aggregate;/* reserved, keep 0 */
+    int32_t unroll;        /* 16-byte fact vectors per thread per step: 1 (default), 2 or 4 */
     int32_t reserved[10];
 } skx_tuning;
 
@@ -184,10 +188,26 @@ skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes,
                                const int32_t *d_measure, int64_t F, const skx_query *q, int64_t *d_out,
                                const skx_tuning *tuning /* NULL = defaults */, void *stream);
 
-/* The tuning skx_probe_aggregate would use for these arguments (defaults or
- * the autotuner's cached choice), written to *out. */
+/* The tuning skx_probe_aggregate would use for these arguments when given
+ * tuning = NULL (the autotuner's cached choice for this shape if there is
+ * one, else the defaults), written to *out. */
 skx_status skx_probe_default_tuning(int32_t N, int32_t row_bytes, int64_t F, const skx_query *q,
                                     int remapped, skx_tuning *out);
+
+/*
+ * Autotuner for the probe (threshold-based processing, Section IV-B, picks t
+ * "experimentally"): runs skx_probe_aggregate with each candidate launch shape
+ * and hot-prefix size on the first min(F, 2^26) rows of the given data,
+ * synchronously on `stream`, and returns the fastest in *out (and its time
+ * scaled to F in *best_ms if not NULL).  remapped = 0 restricts the search to
+ * plain processing (no hot prefix).  d_out (num_groups or 1 int64) is used as
+ * scratch.  The choice is cached per (device, N, row_bytes, agg, log2 F,
+ * remapped); skx_probe_aggregate with tuning = NULL uses the remapped entry
+ * of its shape when present.
+ */
+skx_status skx_probe_autotune(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
+                              const int32_t *d_measure, int64_t F, const skx_query *q, int remapped,
+                              int64_t *d_out, void *stream, skx_tuning *out, float *best_ms);
 
 /* ------------------------------------------------------------------------
  * Whole path from host memory (Sections III-A, III-B and IV in sequence):

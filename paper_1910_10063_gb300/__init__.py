@@ -118,6 +118,9 @@ def lib():
             L.skx_probe_default_tuning.argtypes = [i32, i32, i64, ctypes.POINTER(Query), ctypes.c_int,
                                                    ctypes.POINTER(Tuning)]
             L.skx_probe_default_tuning.restype = st
+            L.skx_probe_autotune.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), ctypes.c_int, P, P,
+                                             ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_float)]
+            L.skx_probe_autotune.restype = st
             L.skx_join_aggregate_host.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), P, P]
             L.skx_join_aggregate_host.restype = st
             _lib = L
@@ -289,6 +292,20 @@ def skx_probe_default_tuning(n: int, row_bytes: int, f: int, query: Query, remap
     _check(lib().skx_probe_default_tuning(n, row_bytes, f, ctypes.byref(query), int(remapped), ctypes.byref(t)),
            "skx_probe_default_tuning")
     return t
+
+
+def skx_probe_autotune(rows, fk, measure, query: Query, remapped: bool = True, out=None, stream=None):
+    """Returns (Tuning, estimated ms for the full F) chosen by timing candidates on this data."""
+    import torch
+    if out is None:
+        out = torch.empty(query.nout, dtype=torch.int64, device=fk.device)
+    t = Tuning()
+    ms = ctypes.c_float()
+    _check(lib().skx_probe_autotune(_dptr(rows, "rows"), rows.shape[0], _row_bytes(rows),
+                                    _dptr(fk, "fk", torch.int32), _dptr(measure, "measure", torch.int32),
+                                    fk.numel(), ctypes.byref(query), int(remapped), _dptr(out, "out", torch.int64),
+                                    _stream(stream), ctypes.byref(t), ctypes.byref(ms)), "skx_probe_autotune")
+    return t, ms.value
 
 
 def skx_join_aggregate_host(rows, fk, measure, query: Query, out=None, stream=None):

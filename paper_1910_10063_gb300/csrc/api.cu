@@ -270,7 +270,7 @@ skx_status skx_probe_default_tuning(int32_t N, int32_t row_bytes, int64_t F, con
     a.F = F;
     a.q = *q;
     skx_tuning t{};
-    if (!remapped) t.hot_keys = -1;
+    if (!cached_probe_tuning(N, row_bytes, *q, F, remapped, &t) && !remapped) t.hot_keys = -1;
     resolve_probe_tuning(a, t);
     *out = t;
     return SKX_OK;
@@ -299,7 +299,10 @@ skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes,
     a.out = d_out;
     a.err = err;
     skx_tuning t{};
-    if (tuning) t = *tuning;
+    if (tuning)
+        t = *tuning;
+    else
+        cached_probe_tuning(N, row_bytes, *q, F, 1, &t);
     resolve_probe_tuning(a, t);
     SKX_CUDA_TRY(launch_probe(a, t, static_cast<cudaStream_t>(stream)));
     return SKX_OK;

@@ -1,32 +1,68 @@
 // histogram.cu -- frequency count of the FK column (the Q3 aggregation that
 // starts the index build, Section III-A): cnt[v] = #{i : fk[i] == v}.
 //
-// GB300 design: the FK column is streamed once with 16-byte loads marked
-// L2 evict-first, so the counter array (4 B per dimension id) stays in L2.
-// Hot keys are the problem under skew (at Zipf s = 1.5 a third of all rows
-// carry the same key): lanes of a warp holding the same key are merged with
-// __match_any_sync and one lane issues a single atomic of the group size,
-// the GPU counterpart of the paper's conflict handling in SIMD aggregation
-// (Section IV-A/IV-B).  Keys outside [0, N) are skipped and flagged.
+// GB300 design.  The FK column is streamed once with 16-byte loads marked L2
+// evict-first, so the counter array (4 B per dimension id) stays in L2.
+// Random atomics into L2 are cheap; what is not cheap is skew: atomics on one
+// address serialise in its L2 slice, and at Zipf s = 1 the hottest key alone
+// takes ~6% of all rows.  So each CTA keeps a small shared-memory cache of
+// keys (open addressing, first come first served): a key that owns a slot is
+// counted with a shared-memory atomic, any other key goes straight to the
+// global counter.  Popular keys show up in the first few hundred rows a CTA
+// sees, so they claim slots at once and never reach L2 again; the slots are
+// flushed with one global atomic each at the end.  Lanes of a warp holding
+// the same key are first merged with __match_any_sync.  This is the paper's
+// hybrid of private buffers for hot items and shared atomics for the rest
+// (Section IV-C), with the hot set discovered on the fly because the build
+// runs before any frequency order exists.  Keys outside [0, N) are skipped
+// and flagged.
 #include "skx_internal.cuh"
 
 namespace skx {
 namespace {
 
 constexpr int kHistBlock = 512;
-constexpr int kHistUnroll = 2;  // 16-byte vectors per lane per iteration
+constexpr int kHistUnroll = 2;     // 16-byte vectors per lane per iteration
+constexpr int kSlotsLog = 12;
+constexpr int kSlots = 1 << kSlotsLog;  // 4096 cached keys per CTA (32 KB)
+constexpr int kProbes = 2;
+constexpr int32_t kEmpty = -1;
 
 __device__ __forceinline__ void count_key(int32_t key, bool valid, int32_t N, uint32_t *__restrict__ cnt,
-                                          unsigned *err) {
+                                          int32_t *s_key, uint32_t *s_cnt, unsigned *err) {
     const bool ok = valid && (uint32_t)key < (uint32_t)N;
     if (valid && !ok) raise_error(err, kErrKeyRange);
-    const unsigned peers = __match_any_sync(0xffffffffu, ok ? key : -1);
-    if (ok && (lane_id() == (unsigned)(__ffs(peers) - 1))) atomicAdd(cnt + key, (uint32_t)__popc(peers));
+    const unsigned peers = __match_any_sync(0xffffffffu, ok ? key : kEmpty);
+    if (!ok || lane_id() != (unsigned)(__ffs(peers) - 1)) return;
+    const uint32_t n = __popc(peers);
+    uint32_t slot = ((uint32_t)key * 0x9E3779B1u) >> (32 - kSlotsLog);
+#pragma unroll
+    for (int p = 0; p < kProbes; ++p) {
+        int32_t owner = s_key[slot];
+        if (owner == kEmpty) {
+            const int32_t prev = atomicCAS(s_key + slot, kEmpty, key);
+            owner = prev == kEmpty ? key : prev;  // claimed now, or taken meanwhile
+        }
+        if (owner == key) {
+            atomicAdd(s_cnt + slot, n);
+            return;
+        }
+        slot = (slot + 1) & (kSlots - 1);
+    }
+    atomicAdd(cnt + key, n);
 }
 
 __global__ void __launch_bounds__(kHistBlock)
     k_histogram(const int32_t *__restrict__ fk, int64_t F, int64_t head, int32_t N, uint32_t *__restrict__ cnt,
                 unsigned *err) {
+    __shared__ int32_t s_key[kSlots];
+    __shared__ uint32_t s_cnt[kSlots];
+    for (int i = threadIdx.x; i < kSlots; i += kHistBlock) {
+        s_key[i] = kEmpty;
+        s_cnt[i] = 0;
+    }
+    __syncthreads();
+
     const uint64_t pol = policy_evict_first();
     const int4 *vec = reinterpret_cast<const int4 *>(fk + head);
     const int64_t nvec = (F - head) >> 2;
@@ -46,10 +82,10 @@ __global__ void __launch_bounds__(kHistBlock)
         }
 #pragma unroll
         for (int u = 0; u < kHistUnroll; ++u) {
-            count_key(k[u].x, v[u], N, cnt, err);
-            count_key(k[u].y, v[u], N, cnt, err);
-            count_key(k[u].z, v[u], N, cnt, err);
-            count_key(k[u].w, v[u], N, cnt, err);
+            count_key(k[u].x, v[u], N, cnt, s_key, s_cnt, err);
+            count_key(k[u].y, v[u], N, cnt, s_key, s_cnt, err);
+            count_key(k[u].z, v[u], N, cnt, s_key, s_cnt, err);
+            count_key(k[u].w, v[u], N, cnt, s_key, s_cnt, err);
         }
     }
     // unaligned head and the ragged tail (fewer than 4 + 3 keys) by warp 0
@@ -60,8 +96,14 @@ __global__ void __launch_bounds__(kHistBlock)
             const int64_t j = j0 + lane;
             const bool valid = j < extra;
             const int64_t idx = j < head ? j : tail0 + (j - head);
-            count_key(valid ? fk[idx] : -1, valid, N, cnt, err);
+            count_key(valid ? fk[idx] : -1, valid, N, cnt, s_key, s_cnt, err);
         }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSlots; i += kHistBlock) {
+        const int32_t key = s_key[i];
+        const uint32_t c = s_cnt[i];
+        if (key != kEmpty && c) atomicAdd(cnt + key, c);
     }
 }
 

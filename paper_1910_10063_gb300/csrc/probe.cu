@@ -92,17 +92,49 @@ __device__ __forceinline__ void fold(const PP &p, const int4 &v, unsigned long l
     }
 }
 
+// Hot-key sums are kept exactly in two 32-bit shared words (32-bit shared
+// atomics run about 4x faster than 64-bit ones on this part): lo accumulates
+// the measures as unsigned 32-bit values, hi counts the wrap-arounds of lo
+// minus the number of negative measures.  Then sum = lo + 2^32 * hi exactly,
+// because a measure m < 0 enters lo as m + 2^32.
+struct HotRef {
+    uint32_t *lo;
+    int32_t *hi;
+};
+
+template <int AGG>
+__device__ __forceinline__ void hot_add(HotRef h, int32_t m) {
+    if (AGG == SKX_AGG_COUNT) {
+        atomicAdd(h.lo, 1u);  // a CTA sees fewer than 2^32 rows
+        return;
+    }
+    const uint32_t u = (uint32_t)m;
+    const uint32_t old = atomicAdd(h.lo, u);
+    const int d = (int)(old + u < old) - (int)(m < 0);
+    if (d) atomicAdd(h.hi, d);
+}
+
+__device__ __forceinline__ unsigned long long hot_value(uint32_t lo, int32_t hi) {
+    return (unsigned long long)lo + ((unsigned long long)(long long)hi << 32);
+}
+
+struct HotArrays {
+    uint32_t *lo, *lane_lo;
+    int32_t *hi, *lane_hi;
+};
+
 template <int AGG, bool FAST16, bool GSMEM>
 __device__ __forceinline__ void handle(const PP &p, int32_t k, int32_t m, const int4 &row, unsigned long long &acc,
-                                       unsigned long long *s_grp, unsigned long long *s_hot,
-                                       unsigned long long *s_lane, unsigned lane) {
-    const unsigned long long amount = AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)m;
+                                       unsigned long long *s_grp, const HotArrays &h, unsigned lane) {
     if ((uint32_t)k < (uint32_t)p.t_hot) {
-        if ((uint32_t)k < (uint32_t)p.t_lane)
-            atomicAdd(s_lane + (size_t(k) << 5) + lane, amount);
-        else
-            atomicAdd(s_hot + k, amount);
+        if ((uint32_t)k < (uint32_t)p.t_lane) {
+            const size_t i = (size_t(k) << 5) + lane;
+            hot_add<AGG>(HotRef{h.lane_lo + i, h.lane_hi + i}, m);
+        } else {
+            hot_add<AGG>(HotRef{h.lo + k, h.hi + k}, m);
+        }
     } else if ((uint32_t)k < (uint32_t)p.N) {
+        const unsigned long long amount = AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)m;
         fold<AGG, GSMEM>(p, row, amount, acc, s_grp);
     } else {
         raise_error(p.err, kErrKeyRange);
@@ -114,9 +146,12 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
     extern __shared__ unsigned long long smem[];
     const int ngrp = GSMEM ? p.G : 0;
     unsigned long long *s_grp = smem;
-    unsigned long long *s_hot = smem + ngrp;
-    unsigned long long *s_lane = s_hot + p.t_hot;
-    const int nsm = ngrp + p.t_hot + (p.t_lane << 5);
+    HotArrays h;
+    h.lo = reinterpret_cast<uint32_t *>(smem + ngrp);
+    h.hi = reinterpret_cast<int32_t *>(h.lo + p.t_hot);
+    h.lane_lo = reinterpret_cast<uint32_t *>(h.hi + p.t_hot);
+    h.lane_hi = reinterpret_cast<int32_t *>(h.lane_lo + (p.t_lane << 5));
+    const int nsm = ngrp + p.t_hot + (p.t_lane << 5);  // 8-byte words
     for (int i = threadIdx.x; i < nsm; i += blockDim.x) smem[i] = 0;
     __syncthreads();
 
@@ -133,20 +168,27 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
 
     if (UNROLL > 0) {
         constexpr int U = UNROLL > 0 ? UNROLL : 1;
+        // software pipeline: the 16-byte fk / measure vectors of the next
+        // iteration are in flight while this iteration's gathers resolve
+        int4 nk[U], nm[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = tid + u * nthr;
+            nk[u] = make_int4(0, 0, 0, 0);
+            nm[u] = make_int4(0, 0, 0, 0);
+            if (i < nvec) {
+                nk[u] = ld_stream16(fk4 + i, pol_s);
+                if (AGG != SKX_AGG_COUNT) nm[u] = ld_stream16(m4 + i, pol_s);
+            }
+        }
         for (int64_t base = tid; base < nvec; base += nthr * U) {
             int32_t key[4 * U], mea[4 * U];
             bool valid[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int64_t i = base + u * nthr;
-                valid[u] = i < nvec;
-                int4 kv = make_int4(0, 0, 0, 0), mv = make_int4(0, 0, 0, 0);
-                if (valid[u]) {
-                    kv = ld_stream16(fk4 + i, pol_s);
-                    if (AGG != SKX_AGG_COUNT) mv = ld_stream16(m4 + i, pol_s);
-                }
-                key[4 * u + 0] = kv.x; key[4 * u + 1] = kv.y; key[4 * u + 2] = kv.z; key[4 * u + 3] = kv.w;
-                mea[4 * u + 0] = mv.x; mea[4 * u + 1] = mv.y; mea[4 * u + 2] = mv.z; mea[4 * u + 3] = mv.w;
+                valid[u] = base + u * nthr < nvec;
+                key[4 * u + 0] = nk[u].x; key[4 * u + 1] = nk[u].y; key[4 * u + 2] = nk[u].z; key[4 * u + 3] = nk[u].w;
+                mea[4 * u + 0] = nm[u].x; mea[4 * u + 1] = nm[u].y; mea[4 * u + 2] = nm[u].z; mea[4 * u + 3] = nm[u].w;
             }
             int4 row[4 * U];
 #pragma unroll
@@ -157,8 +199,16 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
                     row[j] = fetch_row<FAST16, AGG>(p, key[j], pol_g);
             }
 #pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = base + (U + u) * nthr;
+                if (i < nvec) {
+                    nk[u] = ld_stream16(fk4 + i, pol_s);
+                    if (AGG != SKX_AGG_COUNT) nm[u] = ld_stream16(m4 + i, pol_s);
+                }
+            }
+#pragma unroll
             for (int j = 0; j < 4 * U; ++j)
-                if (valid[j / 4]) handle<AGG, FAST16, GSMEM>(p, key[j], mea[j], row[j], acc, s_grp, s_hot, s_lane, lane);
+                if (valid[j / 4]) handle<AGG, FAST16, GSMEM>(p, key[j], mea[j], row[j], acc, s_grp, h, lane);
         }
         // unaligned head (< 4 rows) and ragged tail (< 4 rows)
         if (tid < 8) {
@@ -172,7 +222,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
                 int4 row = make_int4(0, 0, 0, 0);
                 if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N)
                     row = fetch_row<FAST16, AGG>(p, k, pol_g);
-                handle<AGG, FAST16, GSMEM>(p, k, m, row, acc, s_grp, s_hot, s_lane, lane);
+                handle<AGG, FAST16, GSMEM>(p, k, m, row, acc, s_grp, h, lane);
             }
         }
     } else {
@@ -182,17 +232,17 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
             const int32_t m = AGG == SKX_AGG_COUNT ? 0 : ld_stream4(p.measure + i, pol_s);
             int4 row = make_int4(0, 0, 0, 0);
             if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N) row = fetch_row<FAST16, AGG>(p, k, pol_g);
-            handle<AGG, FAST16, GSMEM>(p, k, m, row, acc, s_grp, s_hot, s_lane, lane);
+            handle<AGG, FAST16, GSMEM>(p, k, m, row, acc, s_grp, h, lane);
         }
     }
     __syncthreads();
 
     // hot prefix: one lookup per hot row per CTA
     for (int k = threadIdx.x; k < p.t_hot; k += blockDim.x) {
-        unsigned long long s = s_hot[k];
+        unsigned long long s = hot_value(h.lo[k], h.hi[k]);
         if (k < p.t_lane) {
 #pragma unroll 8
-            for (int l = 0; l < 32; ++l) s += s_lane[(size_t(k) << 5) + l];
+            for (int l = 0; l < 32; ++l) s += hot_value(h.lane_lo[(size_t(k) << 5) + l], h.lane_hi[(size_t(k) << 5) + l]);
         }
         if (s == 0) continue;
         const int4 v = fetch_row<FAST16, AGG>(p, k, pol_g);
@@ -276,32 +326,38 @@ skx_status validate_query(const skx_query *q, int32_t row_bytes) {
     return SKX_OK;
 }
 
+// Fills the defaults of `t` in place.  Idempotent: a resolved tuning resolves
+// to itself ("off" and "as many as fit" are -1, never 0).
 void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t) {
-    if (t.block_threads != 128 && t.block_threads != 256 && t.block_threads != 512)
-        t.block_threads = 512;
-    if (t.unroll != 1 && t.unroll != 2 && t.unroll != 4) t.unroll = 2;
+    if (t.block_threads != 128 && t.block_threads != 256 && t.block_threads != 512) t.block_threads = 512;
+    // one 16-byte vector per thread per step and 1024 threads per SM by default: the
+    // gathers are latency bound, so resident warps matter more than per-thread depth
+    if (t.unroll != 1 && t.unroll != 2 && t.unroll != 4) t.unroll = 1;
+    if (t.ctas_per_sm == 0) t.ctas_per_sm = 1024 / t.block_threads;
+    if (t.ctas_per_sm < 0) t.ctas_per_sm = -1;
+    if (t.hot_keys < 0) {
+        t.hot_keys = -1;
+        t.lane_keys = -1;
+        return;
+    }
     const bool grp = a.q.agg == SKX_AGG_GROUPBY_SUM;
     const int64_t gbytes = (grp && a.q.num_groups <= kMaxSmemGroups) ? int64_t(a.q.num_groups) * 8 : 0;
-    // lane copies
+    const int64_t optin = device_max_smem_optin();
+    if (t.lane_keys == 0) t.lane_keys = 32;
     if (t.lane_keys < 0) t.lane_keys = 0;
-    else if (t.lane_keys == 0) t.lane_keys = 32;
-    // hot prefix sized so that two CTAs fit per SM by default
-    const int64_t budget = (int64_t)device_max_smem_optin() / 2 - 2048;
-    if (t.hot_keys < 0) {
-        t.hot_keys = 0;
-        t.lane_keys = 0;
-    } else {
-        if (t.hot_keys == 0) t.hot_keys = (int32_t)(((budget - gbytes - int64_t(t.lane_keys) * 256) / 8) & ~int64_t(1023));
-        const int64_t room = ((int64_t)device_max_smem_optin() - 1024 - gbytes) / 8;
-        t.hot_keys = clamp32(t.hot_keys, 0, a.N);
-        t.lane_keys = clamp32(t.lane_keys, 0, t.hot_keys);
-        if (int64_t(t.hot_keys) + int64_t(t.lane_keys) * 32 > room) {
-            t.lane_keys = clamp32(t.lane_keys, 0, room / 64);
-            t.hot_keys = clamp32(t.hot_keys, 0, room - int64_t(t.lane_keys) * 32);
-            t.lane_keys = clamp32(t.lane_keys, 0, t.hot_keys);
-        }
+    if (t.hot_keys == 0) {  // sized so that two CTAs fit per SM
+        const int64_t budget = optin / 2 - 2048;
+        t.hot_keys = (int32_t)(((budget - gbytes - int64_t(t.lane_keys) * 256) / 8) & ~int64_t(1023));
     }
-    if (t.ctas_per_sm < 0) t.ctas_per_sm = 0;
+    const int64_t room = (optin - 1024 - gbytes) / 8;  // 8 bytes per hot key, 256 per lane-copied key
+    t.hot_keys = clamp32(t.hot_keys, 1, a.N);
+    t.lane_keys = clamp32(t.lane_keys, 0, t.hot_keys);
+    if (int64_t(t.hot_keys) + int64_t(t.lane_keys) * 32 > room) {
+        t.lane_keys = clamp32(t.lane_keys, 0, room / 64);
+        t.hot_keys = clamp32(t.hot_keys, 1, room - int64_t(t.lane_keys) * 32);
+        t.lane_keys = clamp32(t.lane_keys, 0, t.hot_keys);
+    }
+    if (t.lane_keys == 0) t.lane_keys = -1;
 }
 
 cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t st) {
@@ -317,8 +373,8 @@ cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t s
     p.gcol = a.q.group_col;
     p.G = a.q.agg == SKX_AGG_GROUPBY_SUM ? a.q.num_groups : 1;
     p.pcol = a.q.payload_col;
-    p.t_hot = t.hot_keys;
-    p.t_lane = t.lane_keys;
+    p.t_hot = t.hot_keys > 0 ? t.hot_keys : 0;
+    p.t_lane = t.lane_keys > 0 ? t.lane_keys : 0;
     p.out = reinterpret_cast<unsigned long long *>(a.out);
     p.err = a.err;
     const int nout = a.q.agg == SKX_AGG_GROUPBY_SUM ? a.q.num_groups : 1;
@@ -332,7 +388,7 @@ cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t s
     p.head = mis ? (a.F < 4 - mis ? a.F : 4 - mis) : 0;
     const bool fast16 = a.row_bytes % 16 == 0 && aligned16(a.rows) && p.fcol < 4 && p.gcol < 4 && p.pcol < 4;
     const bool gsmem = a.q.agg == SKX_AGG_GROUPBY_SUM && a.q.num_groups <= kMaxSmemGroups;
-    const size_t smem = size_t((gsmem ? a.q.num_groups : 0) + t.hot_keys + t.lane_keys * 32) * 8;
+    const size_t smem = size_t((gsmem ? a.q.num_groups : 0) + p.t_hot + p.t_lane * 32) * 8;
 
     const bool vec = af == am;
     switch (a.q.agg) {

@@ -34,25 +34,38 @@ __global__ void __launch_bounds__(kRemapBlock)
     const int64_t nvec = (F - head) >> 2;
     const int64_t tid = int64_t(blockIdx.x) * kRemapBlock + threadIdx.x;
     const int64_t nthr = int64_t(gridDim.x) * kRemapBlock;
+    // software pipeline: the next vectors are in flight while this one's rank gathers resolve
+    int4 nk[kRemapUnroll];
+#pragma unroll
+    for (int u = 0; u < kRemapUnroll; ++u) {
+        const int64_t i = tid + u * nthr;
+        if (i < nvec) nk[u] = INPLACE ? ld_stream16_rw(vin + i, pol) : ld_stream16(vin + i, pol);
+    }
     for (int64_t base = tid; base < nvec; base += nthr * kRemapUnroll) {
         int4 k[kRemapUnroll];
 #pragma unroll
+        for (int u = 0; u < kRemapUnroll; ++u) k[u] = nk[u];
+        int4 r[kRemapUnroll];
+#pragma unroll
         for (int u = 0; u < kRemapUnroll; ++u) {
-            const int64_t i = base + u * nthr;
-            // in == out is allowed: each vector is read before it is written by the same thread
-            if (i < nvec) k[u] = INPLACE ? ld_stream16_rw(vin + i, pol) : ld_stream16(vin + i, pol);
+            if (base + u * nthr < nvec) {
+                r[u].x = remap_one(k[u].x, rank, N, err);
+                r[u].y = remap_one(k[u].y, rank, N, err);
+                r[u].z = remap_one(k[u].z, rank, N, err);
+                r[u].w = remap_one(k[u].w, rank, N, err);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kRemapUnroll; ++u) {
+            // in place: vector i + U*nthr is read before any thread writes it (each vector
+            // is read and written by the same thread, in this order)
+            const int64_t i = base + (kRemapUnroll + u) * nthr;
+            if (i < nvec) nk[u] = INPLACE ? ld_stream16_rw(vin + i, pol) : ld_stream16(vin + i, pol);
         }
 #pragma unroll
         for (int u = 0; u < kRemapUnroll; ++u) {
             const int64_t i = base + u * nthr;
-            if (i < nvec) {
-                int4 r;
-                r.x = remap_one(k[u].x, rank, N, err);
-                r.y = remap_one(k[u].y, rank, N, err);
-                r.z = remap_one(k[u].z, rank, N, err);
-                r.w = remap_one(k[u].w, rank, N, err);
-                st_stream16(vout + i, r, pol);
-            }
+            if (i < nvec) st_stream16(vout + i, r[u], pol);
         }
     }
     if (tid < 8) {  // unaligned head (< 4) and ragged tail (< 4)

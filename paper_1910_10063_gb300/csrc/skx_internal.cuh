@@ -132,5 +132,7 @@ struct ProbeArgs {
 void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t);
 cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t st);
 skx_status validate_query(const skx_query *q, int32_t row_bytes);
+// Autotuner cache lookup (autotune.cu).
+bool cached_probe_tuning(int32_t N, int32_t row_bytes, const skx_query &q, int64_t F, int remapped, skx_tuning *out);
 
 }  // namespace skx

@@ -332,3 +332,24 @@ def test_join_aggregate_host_api():
         d = QUERIES[qname]
         got = skx.skx_join_aggregate_host(dim, fk, m, _q(d))
         assert np.array_equal(got, _oracle(dim, fk, m, d))
+
+
+def test_autotune_choice_is_exact_and_cached(probe_data):
+    d = QUERIES["groupby"]
+    want = _oracle(probe_data["dim"], probe_data["fk"], probe_data["m"], d)
+    q = _q(d)
+    for remapped, rows, fk in [(True, probe_data["d_dim2"], probe_data["d_fk2"]),
+                               (False, probe_data["d_dim"], probe_data["d_fk"])]:
+        t, ms = skx.skx_probe_autotune(rows, fk, probe_data["d_m"], q, remapped=remapped)
+        assert ms > 0
+        if not remapped:
+            assert t.hot_keys == -1
+        got = skx.skx_probe_aggregate(rows, fk, probe_data["d_m"], q, tuning=t)
+        assert np.array_equal(got.cpu().numpy(), want)
+    # tuning = NULL picks up the cached remapped choice for this shape
+    dflt = skx.skx_probe_default_tuning(probe_data["d_dim2"].shape[0], 64, probe_data["d_fk2"].numel(), q)
+    t, _ = skx.skx_probe_autotune(probe_data["d_dim2"], probe_data["d_fk2"], probe_data["d_m"], q, remapped=True)
+    dflt = skx.skx_probe_default_tuning(probe_data["d_dim2"].shape[0], 64, probe_data["d_fk2"].numel(), q)
+    assert dflt.as_dict() == t.as_dict()
+    got = skx.skx_probe_aggregate(probe_data["d_dim2"], probe_data["d_fk2"], probe_data["d_m"], q)
+    assert np.array_equal(got.cpu().numpy(), want)
