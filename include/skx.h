@@ -111,6 +111,32 @@ skx_status skx_count(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_coun
 skx_status skx_build_index_from_counts(const uint32_t *d_counts, int32_t N, int64_t F, void *stream,
                                        skx_index **out);
 
+/*
+ * Allocation-free variant of the frequency sort, for callers that must not
+ * allocate device memory when they build the order -- for example because a
+ * framework's caching allocator already holds almost all of HBM, because an
+ * allocation (which can synchronise the device or fail under memory
+ * pressure) is not acceptable in a latency-critical loop, or because the
+ * caller is a plug-in that is handed its buffers and may not call the CUDA
+ * allocator.  The paper has no counterpart; this is a property of this
+ * library's interface only.
+ *
+ * Same result as skx_build_index_from_counts: d_perm[r] (new -> old) and
+ * d_rank[v] (old -> new), int32[N] in caller-owned device buffers, from
+ * d_counts (uint32[N]); F bounds every count.  The scratch space is a fixed
+ * ~16 MiB array inside the library's device image (held by every GPU that
+ * loads the library until the process exits), so N is limited to
+ * skx_sort_by_count_noalloc_max_n() = 2^20 ids; a larger N is rejected
+ * with SKX_EINVAL before anything is enqueued.  The first call on each device
+ * looks up the array's device address (a CUDA runtime call, no allocation),
+ * so make that first call before any stream capture.  All calls share the
+ * one array: calls whose work overlaps on the GPU (different streams, or
+ * different threads) race and must be serialised by the caller.
+ */
+skx_status skx_sort_by_count_noalloc(const uint32_t *d_counts, int32_t N, int64_t F, int32_t *d_perm,
+                                     int32_t *d_rank, void *stream);
+int32_t skx_sort_by_count_noalloc_max_n(void);
+
 /* Borrowed device pointers into the index (valid until skx_index_destroy). */
 skx_status skx_index_perm(const skx_index *idx, const int32_t **d_perm);     /* new -> old, int32[N] */
 skx_status skx_index_rank(const skx_index *idx, const int32_t **d_rank);     /* old -> new, int32[N] */

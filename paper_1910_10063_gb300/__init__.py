@@ -104,6 +104,9 @@ def lib():
             L.skx_count.argtypes = [P, i64, i32, P, P]; L.skx_count.restype = st
             L.skx_build_index_from_counts.argtypes = [P, i32, i64, P, ctypes.POINTER(P)]
             L.skx_build_index_from_counts.restype = st
+            L.skx_sort_by_count_noalloc.argtypes = [P, i32, i64, P, P, P]
+            L.skx_sort_by_count_noalloc.restype = st
+            L.skx_sort_by_count_noalloc_max_n.argtypes = []; L.skx_sort_by_count_noalloc_max_n.restype = i32
             L.skx_kernel_launches.argtypes = []; L.skx_kernel_launches.restype = ctypes.c_uint64
             for n in ("skx_index_perm", "skx_index_rank", "skx_index_counts"):
                 getattr(L, n).argtypes = [P, ctypes.POINTER(P)]
@@ -243,6 +246,18 @@ def skx_build_index_from_counts(counts, f_bound: int, stream=None) -> Index:
     _check(lib().skx_build_index_from_counts(_dptr(counts, "counts", torch.int32), counts.numel(), int(f_bound),
                                              _stream(stream), ctypes.byref(h)), "skx_build_index_from_counts")
     return Index(h, counts.numel())
+
+
+def skx_sort_by_count_noalloc(counts, f_bound: int, perm, rank, stream=None):
+    """Frequency order from counts into caller buffers, without allocating (N <= 2^20)."""
+    import torch
+    n = counts.numel()
+    if perm.numel() != n or rank.numel() != n:
+        raise ValueError("perm and rank must have one entry per id")
+    _check(lib().skx_sort_by_count_noalloc(_dptr(counts, "counts", torch.int32), n, int(f_bound),
+                                           _dptr(perm, "perm", torch.int32), _dptr(rank, "rank", torch.int32),
+                                           _stream(stream)), "skx_sort_by_count_noalloc")
+    return perm, rank
 
 
 def skx_kernel_launches() -> int:

@@ -1,0 +1,84 @@
+// noalloc.cu -- a variant of the frequency sort that allocates nothing.
+//
+// Some callers cannot allocate device memory at the moment they need the
+// index: a process whose framework has already reserved nearly all of HBM in
+// its own caching allocator, a latency-critical loop in which an allocation
+// (which may synchronise the device or fail under memory pressure) is not
+// acceptable, or a plug-in that is handed its buffers and may not touch the
+// CUDA allocator at all.  For them, skx_sort_by_count_noalloc runs the same
+// sort kernels as skx_build_index_from_counts, but its scratch space is a
+// fixed array in this library's device image instead of a stream-ordered
+// allocation.  The caller passes the counts and receives perm and rank in
+// its own buffers.
+//
+// The array holds the scratch of the largest supported domain,
+// N <= kNoAllocMaxN ids (about 16 MiB); every GPU that loads the library
+// keeps it until the process exits.
+#include <mutex>
+
+#include "skx_internal.cuh"
+
+namespace skx {
+namespace {
+
+constexpr int32_t kNoAllocMaxN = 1 << 20;
+
+// Scratch layout of the radix sort for kNoAllocMaxN ids: four 4-byte arrays
+// of N (keys and ids, ping-pong), the per-tile digit counts and the scan's
+// block sums, each rounded up to 256 bytes.  sort_scratch_bytes() is checked
+// against this size on every call.
+constexpr size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kTiles = (size_t(kNoAllocMaxN) + 4095) / 4096;
+constexpr size_t kHistEntries = kTiles * 256;
+constexpr size_t kScanBlocks = (kHistEntries + 4095) / 4096;
+constexpr size_t kNoAllocScratchBytes =
+    up256(up256(up256(up256(up256(up256(4 * size_t(kNoAllocMaxN)) + 4 * size_t(kNoAllocMaxN)) +
+                            4 * size_t(kNoAllocMaxN)) +
+                      4 * size_t(kNoAllocMaxN)) +
+                4 * kHistEntries) +
+          4 * (kScanBlocks + 1));
+
+static __device__ __align__(256) unsigned char g_sort_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_addr[kMaxDevices] = {};  // device address of g_sort_scratch, per device
+
+// The array's name in host code is only a host-side stand-in; the device
+// address is looked up once per device, with that device current.
+skx_status scratch_address(void **out) {
+    int dev = 0;
+    SKX_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return SKX_ENOTSUP;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess || p == nullptr) return cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return SKX_OK;
+}
+
+}  // namespace
+}  // namespace skx
+
+using namespace skx;
+
+extern "C" skx_status skx_sort_by_count_noalloc(const uint32_t *d_counts, int32_t N, int64_t F, int32_t *d_perm,
+                                                int32_t *d_rank, void *stream) {
+    if (N < 1 || F < 0 || F >= (int64_t(1) << 32) || !d_counts || !d_perm || !d_rank) return SKX_EINVAL;
+    if (N > kNoAllocMaxN) return SKX_EINVAL;  // beyond the fixed scratch array
+    if (sort_scratch_bytes(N, F) > kNoAllocScratchBytes) return SKX_EINVAL;
+    void *scratch = nullptr;
+    skx_status s = scratch_address(&scratch);
+    if (s != SKX_OK) return s;
+    // Nothing in the scratch needs to start at zero: every pass fully writes
+    // the digit counts, block sums and key/id arrays before it reads them.
+    SKX_CUDA_TRY(launch_sort_by_count(d_counts, N, F, d_perm, d_rank, scratch, kNoAllocScratchBytes,
+                                      static_cast<cudaStream_t>(stream)));
+    return SKX_OK;
+}
+
+extern "C" int32_t skx_sort_by_count_noalloc_max_n(void) { return kNoAllocMaxN; }
