@@ -237,6 +237,53 @@ def run_ours(a, rank, world, local_rank):
         total_ms = float(t.item())
     result = out.cpu().numpy().copy()
 
+    # ---------------- the same path with the query-specific 8-byte copy (Section III-B)
+    qp = skx.skx_query_prefiltered(q)
+    q8 = torch.empty((a.n, 2), dtype=torch.int32, device=dev)
+    idx0 = skx.skx_build_index(w.fk, a.n)
+    skx.skx_remap(idx0, w.fk, fk2)
+    skx.skx_reorder_query(idx0, w.dim, q, out=q8)
+    tuning_q8, _ = skx.skx_probe_autotune(q8, fk2, w.measure, qp, remapped=True)
+    idx0.close()
+
+    def step_q8(ev):
+        ev[0].record(stream)
+        skx.skx_count(w.fk, a.n, counts)
+        ev[1].record(stream)
+        idx = skx.skx_build_index_from_counts(counts, a.f)
+        ev[2].record(stream)
+        skx.skx_remap(idx, w.fk, fk2)
+        ev[3].record(stream)
+        skx.skx_reorder_query(idx, w.dim, q, out=q8)
+        ev[4].record(stream)
+        skx.skx_probe_aggregate(q8, fk2, w.measure, qp, out=out, tuning=tuning_q8)
+        ev[5].record(stream)
+        return idx
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        step_q8(new_events()).close()
+    evs8 = [new_events() for _ in range(a.steps)]
+    keep = []
+    torch.cuda.synchronize()
+    for k in range(a.steps):
+        flush.zero_()
+        keep.append(step_q8(evs8[k]))
+    torch.cuda.synchronize()
+    for idx in keep:
+        idx.close()
+    if not np.array_equal(out.cpu().numpy(), result):
+        raise RuntimeError("query-copy path disagrees with the whole-row path")
+    ms8 = sum(e[0].elapsed_time(e[5]) for e in evs8)
+    alt_step = {"reorder": "query-specific 8-byte copy {group or sentinel, payload0} (filter applied per dimension row)",
+                "value": round(a.f * a.steps / (ms8 * 1e-3) / 1e9, 3), "unit": UNIT,
+                "ms_per_step": round(ms8 / a.steps, 4),
+                "stages_ms": {s_: round(statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs8), 4)
+                              for i, s_ in enumerate(stages)},
+                "probe_tuning": {k: tuning_q8.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
+                                                                       "hot_keys", "lane_keys")}}
+    del q8
+
     # ---------------- roofline of the dominant kernel
     peak, peak_src = hbm_peak()
     D = expected_distinct(a.n, a.f, a.s)
@@ -281,18 +328,33 @@ def run_ours(a, rank, world, local_rank):
             variants = {"plain": (w.dim, fk_s, t_plain),
                         "remapped_no_hot_prefix": (dim2, fk2, t_lay),
                         "remapped": (dim2, fk2, t_rem)}
+            # narrow query copies (Section III-B), same copy for both layouts
+            qp = skx.skx_query_prefiltered(q)
+            narrow = {}
+            for lay, index, keys in (("plain", None, fk_s), ("remapped", idx, fk2)):
+                c16 = skx.skx_reorder_columns(index, w.dim, [0, 1, 2, 3])
+                q8 = skx.skx_reorder_query(index, w.dim, q)
+                narrow[lay] = (c16, q8, keys)
+            for lay, (c16, q8, keys) in narrow.items():
+                remapped = lay == "remapped"
+                t16, _ = skx.skx_probe_autotune(c16, keys, w.measure, q, remapped=remapped)
+                t8, _ = skx.skx_probe_autotune(q8, keys, w.measure, qp, remapped=remapped)
+                variants[f"{lay}_columns16"] = (c16, keys, t16, q)
+                variants[f"{lay}_query8"] = (q8, keys, t8, qp)
             res, times = {}, {}
-            for name, (rows, keys, tun) in variants.items():
+            for name, v in variants.items():
+                rows, keys, tun = v[:3]
+                qq = v[3] if len(v) > 3 else q
                 o = torch.empty(1000, dtype=torch.int64, device=dev)
                 for _ in range(2):
                     flush.zero_()
-                    skx.skx_probe_aggregate(rows, keys, w.measure, q, out=o, tuning=tun)
+                    skx.skx_probe_aggregate(rows, keys, w.measure, qq, out=o, tuning=tun)
                 ms = []
                 for _ in range(a.sweep_steps):
                     flush.zero_()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    skx.skx_probe_aggregate(rows, keys, w.measure, q, out=o, tuning=tun)
+                    skx.skx_probe_aggregate(rows, keys, w.measure, qq, out=o, tuning=tun)
                     e1.record(stream)
                     e1.synchronize()
                     ms.append(e0.elapsed_time(e1))
@@ -304,13 +366,17 @@ def run_ours(a, rank, world, local_rank):
             entry = {"zipf_s": s, "results_identical": bool(same), "alg_bytes_per_row": round((8 * a.f + 16 * Ds) / a.f, 3)}
             for name, ms in times.items():
                 med = statistics.median(ms)
-                gbs = (8 * a.f + 16 * Ds) / (med * 1e-3) / 1e9
+                gather_b = 8 if name.endswith("query8") else 16
+                gbs = (8 * a.f + gather_b * Ds) / (med * 1e-3) / 1e9
                 tun = variants[name][2]
                 entry[name] = {"ms": round(med, 4), "grows_s": round(a.f / (med * 1e-3) / 1e9, 2),
                                "frac_hbm": round(gbs / peak, 4),
                                "tuning": {k: tun.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
                                                                          "hot_keys", "lane_keys")}}
             entry["speedup_remapped_vs_plain"] = round(entry["plain"]["ms"] / entry["remapped"]["ms"], 3)
+            entry["speedup_columns16"] = round(entry["plain_columns16"]["ms"] / entry["remapped_columns16"]["ms"], 3)
+            entry["speedup_query8"] = round(entry["plain_query8"]["ms"] / entry["remapped_query8"]["ms"], 3)
+            del narrow
             entry["speedup_layout_only"] = round(entry["plain"]["ms"] / entry["remapped_no_hot_prefix"]["ms"], 3)
             sweep.append(entry)
             if s == a.s:
@@ -371,7 +437,7 @@ def run_ours(a, rank, world, local_rank):
         "config": config_of(a, world), "impl": "ours",
         "step": "count -> sort by frequency -> remap fk -> reorder dimension -> probe (filter + GROUP BY SUM)",
         "region_s": round(region_s, 3), "gpu_launches": int(launches),
-        "roofline": roofline, "stages": stage_rep,
+        "roofline": roofline, "stages": stage_rep, "alt_step_query_copy": alt_step,
         "probe_tuning": {k: tuning.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll", "hot_keys",
                                                           "lane_keys")},
         "probe": {"remapped_p50_ms": round(statistics.median(probe_lat), 4) if probe_lat else None,

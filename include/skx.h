@@ -193,6 +193,31 @@ typedef struct skx_query {
     int32_t payload_col; /* column multiplied with the measure, or -1 for 1 */
 } skx_query;
 
+/* ------------------------------------------------------------------------
+ * Query preprocessing copies (Section III-B: "a copy of the needed dimension
+ * table columns for a query, permuted according to the permutation index").
+ * idx may be NULL for the identity order (the same narrow copy of the plain
+ * layout, so that both layouts can be compared on equal terms).
+ *
+ * skx_reorder_columns: row r of d_out is the int32 columns h_cols[0..ncols)
+ *   (a host array, 1 <= ncols <= 16, each < row_bytes/4) of source row
+ *   perm[r] (or r); d_out rows are 4*ncols bytes.
+ * skx_reorder_query: the query's predicate is evaluated once per dimension
+ *   row (as for the Q2 bitmap, Section I) and folded into an 8-byte row
+ *   {key, payload}: key = the group (GROUPBY_SUM) or 0 (COUNT, SUM) when the
+ *   row passes the filter and the sentinel num_groups (or 1) when it does
+ *   not; payload = payload_col (1 for payload_col = -1 or COUNT).  Running
+ *   skx_query_prefiltered(q) over that table gives the result of q.
+ * Input and output must not overlap.
+ * ------------------------------------------------------------------------ */
+skx_status skx_reorder_columns(const skx_index *idx, const void *d_rows_in, int32_t N, int32_t row_bytes,
+                               const int32_t *h_cols, int32_t ncols, void *d_out, void *stream);
+skx_status skx_reorder_query(const skx_index *idx, const void *d_rows_in, int32_t N, int32_t row_bytes,
+                             const skx_query *q, void *d_out, void *stream);
+/* The query to run over a skx_reorder_query table: filter "key < G", group key
+ * (column 0), payload (column 1). */
+skx_query skx_query_prefiltered(const skx_query *q);
+
 /* Launch and threshold parameters; zero-initialise and set what you need.
  * A field left at 0 takes the library default (chosen from N, F, the query
  * and the device).  Resolved values never contain 0: "off" and "as many as
@@ -207,7 +232,9 @@ typedef struct skx_tuning {
                               (default 32); -1 = off */
     int32_t warp_aggregate;/* reserved, keep 0 */
     int32_t unroll;        /* 16-byte fact vectors per thread per step: 1 (default), 2 or 4 */
-    int32_t reserved[10];
+    int32_t gather_policy; /* L2 eviction priority of the dimension gathers: 1 evict_last,
+                              2 evict_normal, 3 evict_first, 4 evict_unchanged (default 2) */
+    int32_t reserved[9];
 } skx_tuning;
 
 skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,

@@ -68,7 +68,7 @@ class Query(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("hot_keys", ctypes.c_int32),
                 ("lane_keys", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32), ("unroll", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("gather_policy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -115,6 +115,10 @@ def lib():
             L.skx_index_destroy.argtypes = [P]; L.skx_index_destroy.restype = None
             L.skx_remap.argtypes = [P, P, P, i64, P]; L.skx_remap.restype = st
             L.skx_reorder.argtypes = [P, P, P, i32, i32, P]; L.skx_reorder.restype = st
+            L.skx_reorder_columns.argtypes = [P, P, i32, i32, P, i32, P, P]; L.skx_reorder_columns.restype = st
+            L.skx_reorder_query.argtypes = [P, P, i32, i32, ctypes.POINTER(Query), P, P]
+            L.skx_reorder_query.restype = st
+            L.skx_query_prefiltered.argtypes = [ctypes.POINTER(Query)]; L.skx_query_prefiltered.restype = Query
             L.skx_probe_aggregate.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), P,
                                               ctypes.POINTER(Tuning), P]
             L.skx_probe_aggregate.restype = st
@@ -285,6 +289,36 @@ def skx_reorder(index: Index, rows_in, rows_out, stream=None):
     _check(lib().skx_reorder(index._h, _dptr(rows_in, "rows_in"), _dptr(rows_out, "rows_out"), rows_in.shape[0],
                              _row_bytes(rows_in), _stream(stream)), "skx_reorder")
     return rows_out
+
+
+def skx_reorder_columns(index: Index | None, rows_in, cols, out=None, stream=None):
+    """Permuted (index) or identity-order (None) copy of the int32 columns `cols` -> int32[N, len(cols)]."""
+    import numpy as np
+    import torch
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    n = rows_in.shape[0]
+    if out is None:
+        out = torch.empty((n, cols.size), dtype=torch.int32, device=rows_in.device)
+    _check(lib().skx_reorder_columns(index._h if index is not None else None, _dptr(rows_in, "rows_in"), n,
+                                     _row_bytes(rows_in), cols.ctypes.data_as(ctypes.c_void_p), cols.size,
+                                     _dptr(out, "out"), _stream(stream)), "skx_reorder_columns")
+    return out
+
+
+def skx_reorder_query(index: Index | None, rows_in, query: Query, out=None, stream=None):
+    """8-byte {key or sentinel, payload} rows with the query's filter applied -> int32[N, 2]."""
+    import torch
+    n = rows_in.shape[0]
+    if out is None:
+        out = torch.empty((n, 2), dtype=torch.int32, device=rows_in.device)
+    _check(lib().skx_reorder_query(index._h if index is not None else None, _dptr(rows_in, "rows_in"), n,
+                                   _row_bytes(rows_in), ctypes.byref(query), _dptr(out, "out"), _stream(stream)),
+           "skx_reorder_query")
+    return out
+
+
+def skx_query_prefiltered(query: Query) -> Query:
+    return lib().skx_query_prefiltered(ctypes.byref(query))
 
 
 def skx_probe_aggregate(rows, fk, measure, query: Query, out=None, tuning: Tuning | None = None, stream=None):

@@ -259,6 +259,46 @@ skx_status skx_reorder(const skx_index *idx, const void *d_rows_in, void *d_rows
     return SKX_OK;
 }
 
+skx_status skx_reorder_columns(const skx_index *idx, const void *d_rows_in, int32_t N, int32_t row_bytes,
+                               const int32_t *h_cols, int32_t ncols, void *d_out, void *stream) {
+    if (N < 1 || row_bytes <= 0 || row_bytes % 4 != 0 || !d_rows_in || !d_out || !h_cols || ncols < 1 || ncols > 16)
+        return SKX_EINVAL;
+    if (idx && idx->N != N) return SKX_EINVAL;
+    if (!valid_stream_ptrs(d_rows_in) || !valid_stream_ptrs(d_out)) return SKX_EINVAL;
+    for (int i = 0; i < ncols; ++i)
+        if (h_cols[i] < 0 || h_cols[i] >= row_bytes / 4) return SKX_EINVAL;
+    const char *a = static_cast<const char *>(d_rows_in), *b = static_cast<const char *>(d_out);
+    if (a < b + int64_t(N) * ncols * 4 && b < a + int64_t(N) * row_bytes) return SKX_EINVAL;
+    SKX_CUDA_TRY(launch_reorder_columns(idx ? idx->perm : nullptr, N, d_rows_in, row_bytes, h_cols, ncols, d_out,
+                                        static_cast<cudaStream_t>(stream)));
+    return SKX_OK;
+}
+
+skx_status skx_reorder_query(const skx_index *idx, const void *d_rows_in, int32_t N, int32_t row_bytes,
+                             const skx_query *q, void *d_out, void *stream) {
+    skx_status s = validate_query(q, row_bytes);
+    if (s != SKX_OK) return s;
+    if (N < 1 || !d_rows_in || !d_out || (idx && idx->N != N)) return SKX_EINVAL;
+    if (!valid_stream_ptrs(d_rows_in) || (reinterpret_cast<uintptr_t>(d_out) & 7u)) return SKX_EINVAL;
+    const char *a = static_cast<const char *>(d_rows_in), *b = static_cast<const char *>(d_out);
+    if (a < b + int64_t(N) * 8 && b < a + int64_t(N) * row_bytes) return SKX_EINVAL;
+    SKX_CUDA_TRY(launch_reorder_query(idx ? idx->perm : nullptr, N, d_rows_in, row_bytes, *q, d_out,
+                                      static_cast<cudaStream_t>(stream)));
+    return SKX_OK;
+}
+
+skx_query skx_query_prefiltered(const skx_query *q) {
+    skx_query r{};
+    if (!q) return r;
+    r.agg = q->agg;
+    r.num_groups = q->agg == SKX_AGG_GROUPBY_SUM ? q->num_groups : 1;
+    r.filter_col = 0;
+    r.filter_lt = r.num_groups;  // the sentinel num_groups fails "key < num_groups"
+    r.group_col = 0;
+    r.payload_col = 1;
+    return r;
+}
+
 skx_status skx_probe_default_tuning(int32_t N, int32_t row_bytes, int64_t F, const skx_query *q, int remapped,
                                     skx_tuning *out) {
     if (!out || N < 1 || F < 0) return SKX_EINVAL;

@@ -10,8 +10,7 @@
 // counted with a shared-memory atomic, any other key goes straight to the
 // global counter.  Popular keys show up in the first few hundred rows a CTA
 // sees, so they claim slots at once and never reach L2 again; the slots are
-// flushed with one global atomic each at the end.  Lanes of a warp holding
-// the same key are first merged with __match_any_sync.  This is the paper's
+// flushed with one global atomic each at the end.  This is the paper's
 // hybrid of private buffers for hot items and shared atomics for the rest
 // (Section IV-C), with the hot set discovered on the fly because the build
 // runs before any frequency order exists.  Keys outside [0, N) are skipped
@@ -30,11 +29,11 @@ constexpr int32_t kEmpty = -1;
 
 __device__ __forceinline__ void count_key(int32_t key, bool valid, int32_t N, uint32_t *__restrict__ cnt,
                                           int32_t *s_key, uint32_t *s_cnt, unsigned *err) {
-    const bool ok = valid && (uint32_t)key < (uint32_t)N;
-    if (valid && !ok) raise_error(err, kErrKeyRange);
-    const unsigned peers = __match_any_sync(0xffffffffu, ok ? key : kEmpty);
-    if (!ok || lane_id() != (unsigned)(__ffs(peers) - 1)) return;
-    const uint32_t n = __popc(peers);
+    if (!valid) return;
+    if ((uint32_t)key >= (uint32_t)N) {
+        raise_error(err, kErrKeyRange);
+        return;
+    }
     uint32_t slot = ((uint32_t)key * 0x9E3779B1u) >> (32 - kSlotsLog);
 #pragma unroll
     for (int p = 0; p < kProbes; ++p) {
@@ -44,12 +43,12 @@ __device__ __forceinline__ void count_key(int32_t key, bool valid, int32_t N, ui
             owner = prev == kEmpty ? key : prev;  // claimed now, or taken meanwhile
         }
         if (owner == key) {
-            atomicAdd(s_cnt + slot, n);
+            atomicAdd(s_cnt + slot, 1u);
             return;
         }
         slot = (slot + 1) & (kSlots - 1);
     }
-    atomicAdd(cnt + key, n);
+    atomicAdd(cnt + key, 1u);
 }
 
 __global__ void __launch_bounds__(kHistBlock)

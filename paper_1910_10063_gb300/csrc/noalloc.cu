@@ -23,20 +23,8 @@ namespace {
 
 constexpr int32_t kNoAllocMaxN = 1 << 20;
 
-// Scratch layout of the radix sort for kNoAllocMaxN ids: four 4-byte arrays
-// of N (keys and ids, ping-pong), the per-tile digit counts and the scan's
-// block sums, each rounded up to 256 bytes.  sort_scratch_bytes() is checked
-// against this size on every call.
-constexpr size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
-constexpr size_t kTiles = (size_t(kNoAllocMaxN) + 4095) / 4096;
-constexpr size_t kHistEntries = kTiles * 256;
-constexpr size_t kScanBlocks = (kHistEntries + 4095) / 4096;
-constexpr size_t kNoAllocScratchBytes =
-    up256(up256(up256(up256(up256(up256(4 * size_t(kNoAllocMaxN)) + 4 * size_t(kNoAllocMaxN)) +
-                            4 * size_t(kNoAllocMaxN)) +
-                      4 * size_t(kNoAllocMaxN)) +
-                4 * kHistEntries) +
-          4 * (kScanBlocks + 1));
+// Scratch of the radix sort for kNoAllocMaxN ids (about 16 MiB).
+constexpr size_t kNoAllocScratchBytes = sort_scratch_bound(size_t(kNoAllocMaxN));
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kNoAllocScratchBytes];
 

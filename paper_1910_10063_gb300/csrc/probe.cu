@@ -37,6 +37,7 @@ struct PP {
     int32_t N, row_bytes;
     int32_t fcol, flt, gcol, G, pcol;
     int32_t t_hot, t_lane;
+    int32_t gather_policy;
     unsigned long long *out;
     unsigned *err;
 };
@@ -45,12 +46,29 @@ __device__ __forceinline__ int sel4(const int4 &v, int c) {
     return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 
+__device__ __forceinline__ int2 ld_gather8(const int2 *p, uint64_t pol) {
+    int2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.s32 {%0,%1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ int sel2(const int2 &v, int c) { return c == 0 ? v.x : v.y; }
+
+// Row access paths: 16-byte rows (or wider, columns in the first 16 bytes),
+// 8-byte rows, or one 4-byte load per needed column.
+enum RowPath { kRowGeneric = 0, kRow16 = 1, kRow8 = 2 };
+
 // Gathered values of one dimension row: x = filter column, y = group column, z = payload.
-template <bool FAST16, int AGG>
+template <int PATH, int AGG>
 __device__ __forceinline__ int4 fetch_row(const PP &p, int32_t k, uint64_t pol) {
     const char *r = p.rows + size_t(k) * size_t(p.row_bytes);
     int4 v;
-    if (FAST16) {
+    if (PATH == kRow8) {
+        const int2 raw = ld_gather8(reinterpret_cast<const int2 *>(r), pol);
+        v.x = p.fcol >= 0 ? sel2(raw, p.fcol) : 0;
+        v.y = AGG == SKX_AGG_GROUPBY_SUM ? sel2(raw, p.gcol) : 0;
+        v.z = p.pcol >= 0 ? sel2(raw, p.pcol) : 1;
+    } else if (PATH == kRow16) {
         const int4 raw = ld_gather16(reinterpret_cast<const int4 *>(r), pol);
         v.x = p.fcol >= 0 ? sel4(raw, p.fcol) : 0;
         v.y = AGG == SKX_AGG_GROUPBY_SUM ? sel4(raw, p.gcol) : 0;
@@ -123,7 +141,7 @@ struct HotArrays {
     int32_t *hi, *lane_hi;
 };
 
-template <int AGG, bool FAST16, bool GSMEM>
+template <int AGG, int PATH, bool GSMEM>
 __device__ __forceinline__ void handle(const PP &p, int32_t k, int32_t m, const int4 &row, unsigned long long &acc,
                                        unsigned long long *s_grp, const HotArrays &h, unsigned lane) {
     if ((uint32_t)k < (uint32_t)p.t_hot) {
@@ -141,7 +159,7 @@ __device__ __forceinline__ void handle(const PP &p, int32_t k, int32_t m, const 
     }
 }
 
-template <int AGG, bool FAST16, bool GSMEM, int UNROLL>
+template <int AGG, int PATH, bool GSMEM, int UNROLL>
 __global__ void __launch_bounds__(512) k_probe(PP p) {
     extern __shared__ unsigned long long smem[];
     const int ngrp = GSMEM ? p.G : 0;
@@ -156,7 +174,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
     __syncthreads();
 
     const uint64_t pol_s = policy_evict_first();
-    const uint64_t pol_g = policy_evict_last();
+    const uint64_t pol_g = policy_by_code(p.gather_policy);
     const unsigned lane = lane_id();
     unsigned long long acc = 0;
 
@@ -196,7 +214,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
                 const uint32_t k = (uint32_t)key[j];
                 row[j] = make_int4(0, 0, 0, 0);
                 if (valid[j / 4] && k >= (uint32_t)p.t_hot && k < (uint32_t)p.N)
-                    row[j] = fetch_row<FAST16, AGG>(p, key[j], pol_g);
+                    row[j] = fetch_row<PATH, AGG>(p, key[j], pol_g);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -208,7 +226,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
             }
 #pragma unroll
             for (int j = 0; j < 4 * U; ++j)
-                if (valid[j / 4]) handle<AGG, FAST16, GSMEM>(p, key[j], mea[j], row[j], acc, s_grp, h, lane);
+                if (valid[j / 4]) handle<AGG, PATH, GSMEM>(p, key[j], mea[j], row[j], acc, s_grp, h, lane);
         }
         // unaligned head (< 4 rows) and ragged tail (< 4 rows)
         if (tid < 8) {
@@ -221,8 +239,8 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
                 const int32_t m = AGG == SKX_AGG_COUNT ? 0 : p.measure[idx];
                 int4 row = make_int4(0, 0, 0, 0);
                 if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N)
-                    row = fetch_row<FAST16, AGG>(p, k, pol_g);
-                handle<AGG, FAST16, GSMEM>(p, k, m, row, acc, s_grp, h, lane);
+                    row = fetch_row<PATH, AGG>(p, k, pol_g);
+                handle<AGG, PATH, GSMEM>(p, k, m, row, acc, s_grp, h, lane);
             }
         }
     } else {
@@ -231,8 +249,8 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
             const int32_t k = ld_stream4(p.fk + i, pol_s);
             const int32_t m = AGG == SKX_AGG_COUNT ? 0 : ld_stream4(p.measure + i, pol_s);
             int4 row = make_int4(0, 0, 0, 0);
-            if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N) row = fetch_row<FAST16, AGG>(p, k, pol_g);
-            handle<AGG, FAST16, GSMEM>(p, k, m, row, acc, s_grp, h, lane);
+            if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N) row = fetch_row<PATH, AGG>(p, k, pol_g);
+            handle<AGG, PATH, GSMEM>(p, k, m, row, acc, s_grp, h, lane);
         }
     }
     __syncthreads();
@@ -245,7 +263,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
             for (int l = 0; l < 32; ++l) s += hot_value(h.lane_lo[(size_t(k) << 5) + l], h.lane_hi[(size_t(k) << 5) + l]);
         }
         if (s == 0) continue;
-        const int4 v = fetch_row<FAST16, AGG>(p, k, pol_g);
+        const int4 v = fetch_row<PATH, AGG>(p, k, pol_g);
         fold<AGG, GSMEM>(p, v, s, acc, s_grp);
     }
 
@@ -262,9 +280,9 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
     }
 }
 
-template <int AGG, bool FAST16, bool GSMEM, int UNROLL>
+template <int AGG, int PATH, bool GSMEM, int UNROLL>
 cudaError_t launch_one(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st) {
-    auto kern = k_probe<AGG, FAST16, GSMEM, UNROLL>;
+    auto kern = k_probe<AGG, PATH, GSMEM, UNROLL>;
     static int configured_smem = -1;  // per instantiation; the device limit is the same for all GB300s
     const int want = device_max_smem_optin();
     if (configured_smem != want) {
@@ -288,25 +306,30 @@ cudaError_t launch_one(const PP &p, const skx_tuning &t, size_t smem, cudaStream
     return cudaGetLastError();
 }
 
-template <int AGG, bool FAST16, bool GSMEM>
+template <int AGG, int PATH, bool GSMEM>
 cudaError_t launch_unroll(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st, bool vec) {
-    if (!vec) return launch_one<AGG, FAST16, GSMEM, 0>(p, t, smem, st);
+    if (!vec) return launch_one<AGG, PATH, GSMEM, 0>(p, t, smem, st);
     switch (t.unroll) {
-        case 1: return launch_one<AGG, FAST16, GSMEM, 1>(p, t, smem, st);
-        case 4: return launch_one<AGG, FAST16, GSMEM, 4>(p, t, smem, st);
-        default: return launch_one<AGG, FAST16, GSMEM, 2>(p, t, smem, st);
+        case 1: return launch_one<AGG, PATH, GSMEM, 1>(p, t, smem, st);
+        case 4: return launch_one<AGG, PATH, GSMEM, 4>(p, t, smem, st);
+        default: return launch_one<AGG, PATH, GSMEM, 2>(p, t, smem, st);
     }
 }
 
 template <int AGG>
-cudaError_t launch_agg(const PP &p, bool fast16, bool gsmem, const skx_tuning &t, size_t smem, cudaStream_t st,
+cudaError_t launch_agg(const PP &p, int path, bool gsmem, const skx_tuning &t, size_t smem, cudaStream_t st,
                        bool vec) {
-    if (fast16) {
-        if (gsmem) return launch_unroll<AGG, true, true>(p, t, smem, st, vec);
-        return launch_unroll<AGG, true, false>(p, t, smem, st, vec);
+    if (AGG != SKX_AGG_GROUPBY_SUM) gsmem = false;  // COUNT and SUM accumulate in registers
+    if (path == kRow16) {
+        if (gsmem) return launch_unroll<AGG, kRow16, true>(p, t, smem, st, vec);
+        return launch_unroll<AGG, kRow16, false>(p, t, smem, st, vec);
     }
-    if (gsmem) return launch_unroll<AGG, false, true>(p, t, smem, st, vec);
-    return launch_unroll<AGG, false, false>(p, t, smem, st, vec);
+    if (path == kRow8) {
+        if (gsmem) return launch_unroll<AGG, kRow8, true>(p, t, smem, st, vec);
+        return launch_unroll<AGG, kRow8, false>(p, t, smem, st, vec);
+    }
+    if (gsmem) return launch_unroll<AGG, kRowGeneric, true>(p, t, smem, st, vec);
+    return launch_unroll<AGG, kRowGeneric, false>(p, t, smem, st, vec);
 }
 
 int32_t clamp32(int64_t v, int64_t lo, int64_t hi) { return (int32_t)(v < lo ? lo : (v > hi ? hi : v)); }
@@ -335,6 +358,7 @@ void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t) {
     if (t.unroll != 1 && t.unroll != 2 && t.unroll != 4) t.unroll = 1;
     if (t.ctas_per_sm == 0) t.ctas_per_sm = 1024 / t.block_threads;
     if (t.ctas_per_sm < 0) t.ctas_per_sm = -1;
+    if (t.gather_policy < 1 || t.gather_policy > 4) t.gather_policy = 2;
     if (t.hot_keys < 0) {
         t.hot_keys = -1;
         t.lane_keys = -1;
@@ -375,6 +399,7 @@ cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t s
     p.pcol = a.q.payload_col;
     p.t_hot = t.hot_keys > 0 ? t.hot_keys : 0;
     p.t_lane = t.lane_keys > 0 ? t.lane_keys : 0;
+    p.gather_policy = t.gather_policy;
     p.out = reinterpret_cast<unsigned long long *>(a.out);
     p.err = a.err;
     const int nout = a.q.agg == SKX_AGG_GROUPBY_SUM ? a.q.num_groups : 1;
@@ -386,15 +411,20 @@ cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t s
     const uintptr_t am = a.q.agg == SKX_AGG_COUNT ? af : (reinterpret_cast<uintptr_t>(a.measure) & 15u);
     const int64_t mis = (int64_t)(af >> 2);
     p.head = mis ? (a.F < 4 - mis ? a.F : 4 - mis) : 0;
-    const bool fast16 = a.row_bytes % 16 == 0 && aligned16(a.rows) && p.fcol < 4 && p.gcol < 4 && p.pcol < 4;
+    int path = kRowGeneric;
+    if (a.row_bytes % 16 == 0 && aligned16(a.rows) && p.fcol < 4 && p.gcol < 4 && p.pcol < 4)
+        path = kRow16;
+    else if (a.row_bytes == 8 && (reinterpret_cast<uintptr_t>(a.rows) & 7u) == 0 && p.fcol < 2 && p.gcol < 2 &&
+             p.pcol < 2)
+        path = kRow8;
     const bool gsmem = a.q.agg == SKX_AGG_GROUPBY_SUM && a.q.num_groups <= kMaxSmemGroups;
     const size_t smem = size_t((gsmem ? a.q.num_groups : 0) + p.t_hot + p.t_lane * 32) * 8;
 
     const bool vec = af == am;
     switch (a.q.agg) {
-        case SKX_AGG_COUNT: return launch_agg<SKX_AGG_COUNT>(p, fast16, gsmem, t, smem, st, vec);
-        case SKX_AGG_SUM: return launch_agg<SKX_AGG_SUM>(p, fast16, gsmem, t, smem, st, vec);
-        default: return launch_agg<SKX_AGG_GROUPBY_SUM>(p, fast16, gsmem, t, smem, st, vec);
+        case SKX_AGG_COUNT: return launch_agg<SKX_AGG_COUNT>(p, path, gsmem, t, smem, st, vec);
+        case SKX_AGG_SUM: return launch_agg<SKX_AGG_SUM>(p, path, gsmem, t, smem, st, vec);
+        default: return launch_agg<SKX_AGG_GROUPBY_SUM>(p, path, gsmem, t, smem, st, vec);
     }
 }
 

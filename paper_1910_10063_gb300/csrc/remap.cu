@@ -98,6 +98,57 @@ __global__ void __launch_bounds__(512)
     }
 }
 
+// Permuted copy of selected columns (Section III-B): out[r][c] = in[src(r)][cols[c]],
+// src(r) = perm[r] (or r when perm is null: the identity-order copy of the plain layout).
+struct ColList {
+    int32_t c[16];
+};
+
+template <int NC>
+__global__ void __launch_bounds__(512)
+    k_reorder_cols(const int32_t *__restrict__ perm, int32_t N, const int32_t *__restrict__ in, int32_t words,
+                   ColList cols, int32_t ncols, int32_t *__restrict__ out) {
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < N; r += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t src = perm ? __ldg(perm + r) : (int32_t)r;
+        if ((uint32_t)src >= (uint32_t)N) continue;
+        const int32_t *row = in + int64_t(src) * words;
+        if (NC == 4) {
+            int4 v;
+            v.x = __ldg(row + cols.c[0]);
+            v.y = __ldg(row + cols.c[1]);
+            v.z = __ldg(row + cols.c[2]);
+            v.w = __ldg(row + cols.c[3]);
+            reinterpret_cast<int4 *>(out)[r] = v;
+        } else if (NC == 2) {
+            int2 v;
+            v.x = __ldg(row + cols.c[0]);
+            v.y = __ldg(row + cols.c[1]);
+            reinterpret_cast<int2 *>(out)[r] = v;
+        } else {
+            for (int c = 0; c < ncols; ++c) out[r * ncols + c] = __ldg(row + cols.c[c]);
+        }
+    }
+}
+
+// Query-specific copy (Sections I and III-B): the predicate is evaluated once per
+// dimension row, as for the Q2 bitmap, and folded into the copy:
+// out[r] = {passes ? group : sentinel, payload}.
+__global__ void __launch_bounds__(512)
+    k_reorder_query(const int32_t *__restrict__ perm, int32_t N, const int32_t *__restrict__ in, int32_t words,
+                    int32_t fcol, int32_t flt, int32_t gcol, int32_t pcol, int32_t sentinel,
+                    int2 *__restrict__ out) {
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < N; r += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t src = perm ? __ldg(perm + r) : (int32_t)r;
+        if ((uint32_t)src >= (uint32_t)N) continue;
+        const int32_t *row = in + int64_t(src) * words;
+        const bool pass = fcol < 0 || __ldg(row + fcol) < flt;
+        int2 v;
+        v.x = pass ? (gcol >= 0 ? __ldg(row + gcol) : 0) : sentinel;
+        v.y = pcol >= 0 ? __ldg(row + pcol) : 1;
+        out[r] = v;
+    }
+}
+
 int grid_for(int64_t work_items, int block, int per_sm) {
     const int sms = device_sm_count();
     int64_t want = (work_items + block - 1) / block;
@@ -124,6 +175,37 @@ cudaError_t launch_remap(const int32_t *d_rank, int32_t N, const int32_t *d_in, 
         k_remap<true><<<grid, kRemapBlock, 0, st>>>(d_rank, N, d_in, d_out, F, head, d_err);
     else
         k_remap<false><<<grid, kRemapBlock, 0, st>>>(d_rank, N, d_in, d_out, F, head, d_err);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder_columns(const int32_t *d_perm, int32_t N, const void *d_in, int32_t row_bytes,
+                                   const int32_t *cols, int32_t ncols, void *d_out, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    ColList cl{};
+    for (int i = 0; i < ncols; ++i) cl.c[i] = cols[i];
+    const int32_t words = row_bytes / 4;
+    const int grid = grid_for(N, 512, 4);
+    const int32_t *in = static_cast<const int32_t *>(d_in);
+    int32_t *out = static_cast<int32_t *>(d_out);
+    if (ncols == 4 && aligned16(d_out))
+        k_reorder_cols<4><<<grid, 512, 0, st>>>(d_perm, N, in, words, cl, ncols, out);
+    else if (ncols == 2 && (reinterpret_cast<uintptr_t>(d_out) & 7u) == 0)
+        k_reorder_cols<2><<<grid, 512, 0, st>>>(d_perm, N, in, words, cl, ncols, out);
+    else
+        k_reorder_cols<0><<<grid, 512, 0, st>>>(d_perm, N, in, words, cl, ncols, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder_query(const int32_t *d_perm, int32_t N, const void *d_in, int32_t row_bytes,
+                                 const skx_query &q, void *d_out, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const bool grp = q.agg == SKX_AGG_GROUPBY_SUM;
+    const int32_t sentinel = grp ? q.num_groups : 1;
+    k_reorder_query<<<grid_for(N, 512, 4), 512, 0, st>>>(
+        d_perm, N, static_cast<const int32_t *>(d_in), row_bytes / 4, q.filter_col, q.filter_lt,
+        grp ? q.group_col : -1, q.agg == SKX_AGG_COUNT ? -1 : q.payload_col, sentinel, static_cast<int2 *>(d_out));
     note_launches(1);
     return cudaGetLastError();
 }

@@ -53,6 +53,26 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
     return p;
 }
 
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_unchanged() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_unchanged.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// 1 evict_last, 2 evict_normal, 3 evict_first, 4 evict_unchanged
+__device__ __forceinline__ uint64_t policy_by_code(int code) {
+    switch (code) {
+        case 1: return policy_evict_last();
+        case 3: return policy_evict_first();
+        case 4: return policy_evict_unchanged();
+        default: return policy_evict_normal();
+    }
+}
+
 // 16-byte streaming load: read-only path, no L1 allocation, L2 evict-first.
 __device__ __forceinline__ int4 ld_stream16(const int4 *p, uint64_t pol) {
     int4 v;
@@ -108,7 +128,18 @@ __device__ __forceinline__ void raise_error(unsigned *err, unsigned bit) {
 cudaError_t launch_histogram(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_cnt, unsigned *d_err,
                              cudaStream_t st);
 
-// Scratch bytes the frequency sort needs for N ids and F rows.
+// Scratch bytes the frequency sort needs for n ids: four 4-byte arrays of n
+// (keys and ids, ping-pong), the per-tile digit counts (256 per 4096-id tile),
+// the scan's block sums and one word for the heavy-id count, each rounded up
+// to 256 bytes.  sort.cu lays its scratch out in exactly this order.
+constexpr size_t sort_up256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t sort_scratch_bound(size_t n) {
+    return sort_up256(sort_up256(sort_up256(sort_up256(sort_up256(sort_up256(sort_up256(4 * n) + 4 * n) + 4 * n) +
+                                                      4 * n) +
+                                            4 * (((n + 4095) / 4096) * 256)) +
+                                 4 * ((((n + 4095) / 4096) * 256 + 4095) / 4096 + 1)) +
+                      4);
+}
 size_t sort_scratch_bytes(int32_t N, int64_t F);
 // Sorts ids by (cnt desc, id asc): writes perm (new->old) and rank (old->new).
 cudaError_t launch_sort_by_count(const uint32_t *d_cnt, int32_t N, int64_t F, int32_t *d_perm, int32_t *d_rank,
@@ -118,6 +149,10 @@ cudaError_t launch_remap(const int32_t *d_rank, int32_t N, const int32_t *d_in, 
                          unsigned *d_err, cudaStream_t st);
 cudaError_t launch_reorder(const int32_t *d_perm, int32_t N, const void *d_in, void *d_out, int32_t row_bytes,
                            cudaStream_t st);
+cudaError_t launch_reorder_columns(const int32_t *d_perm, int32_t N, const void *d_in, int32_t row_bytes,
+                                   const int32_t *cols, int32_t ncols, void *d_out, cudaStream_t st);
+cudaError_t launch_reorder_query(const int32_t *d_perm, int32_t N, const void *d_in, int32_t row_bytes,
+                                 const skx_query &q, void *d_out, cudaStream_t st);
 
 struct ProbeArgs {
     const void *rows;

@@ -13,6 +13,17 @@
 // a tile comes from processing each warp's 512 keys in 32-key rounds in
 // order, ranking equal digits with __match_any_sync.  The final pass writes
 // perm[pos] = id and rank[id] = pos directly.
+//
+// Skewed counts are mostly small: under Zipf most ids occur fewer than 255
+// times.  So when the average count F/N is small, one stable pass on the
+// clamped digit 255 - min(count, 255) already puts every id with count < 255
+// at its final place (written straight to perm and rank), and collects the
+// "heavy" ids (count >= 255, at most F/255 of them) in ascending id order at
+// the front.  Only that heavy prefix, whose length H is known on the device
+// alone, goes through the full multi-pass sort; those kernels read H from
+// device memory and their grids are sized for the bound F/255.
+#include <algorithm>
+
 #include "skx_internal.cuh"
 
 namespace skx {
@@ -29,25 +40,67 @@ constexpr int kScanTile = kSortBlock * kScanItems;  // 4096
 
 __device__ __forceinline__ uint32_t first_key(const uint32_t *cnt, uint32_t i) { return ~cnt[i]; }
 
-// ------------------------------------------------------------------ upsweep
-template <bool FIRST>
+// Key sources of a pass.
+enum KeySrc {
+    kSrcClamped = 0,  // key = 255 - min(cnt[i], 255), id = i     (the heavy/light split pass)
+    kSrcCounts = 1,   // key = ~cnt[i], id = i                     (first pass of the plain sort)
+    kSrcPairs = 2,    // key = keys_in[i], id = vals_in[i]         (later passes)
+    kSrcGather = 3,   // id = vals_in[i], key = ~cnt[id]           (first pass over the heavy ids)
+};
+// Outputs of a pass.
+enum Out {
+    kOutPairs = 0,  // keys_out[pos], vals_out[pos]
+    kOutFinal = 1,  // perm[pos] = id, rank[id] = pos
+    kOutSplit = 2,  // digit 0 (heavy): vals_out[pos] = id; other digits: final
+};
+
+template <int SRC>
+__device__ __forceinline__ void load_key(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ keys_in,
+                                         const uint32_t *__restrict__ vals_in, uint32_t i, uint32_t &key,
+                                         uint32_t &val) {
+    if (SRC == kSrcClamped) {
+        const uint32_t c = cnt[i];
+        key = 255u - (c < 255u ? c : 255u);
+        val = i;
+    } else if (SRC == kSrcCounts) {
+        key = ~cnt[i];
+        val = i;
+    } else if (SRC == kSrcPairs) {
+        key = keys_in[i];
+        val = vals_in[i];
+    } else {
+        val = vals_in[i];
+        key = ~cnt[val];
+    }
+}
+
+// n_dev != null: the element count is read from the device (heavy passes).
+template <int SRC>
 __global__ void __launch_bounds__(kSortBlock)
-    k_radix_upsweep(const uint32_t *__restrict__ keys, uint32_t n, int shift, uint32_t *__restrict__ tile_hist,
-                    uint32_t num_tiles) {
+    k_radix_upsweep(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ keys_in,
+                    const uint32_t *__restrict__ vals_in, uint32_t n_host, const uint32_t *__restrict__ n_dev,
+                    int shift, uint32_t *__restrict__ tile_hist, uint32_t num_tiles) {
     __shared__ uint32_t s_cnt[kWarps][kBins];
+    const uint32_t n = n_dev ? *n_dev : n_host;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     for (int i = threadIdx.x; i < kWarps * kBins; i += kSortBlock) (&s_cnt[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = blockIdx.x;
     const uint32_t base = tile * kTile + warp * (32 * kRounds);
+    if (tile * kTile < n) {  // tiles past the end (heavy passes) publish zero counts
 #pragma unroll 4
-    for (int r = 0; r < kRounds; ++r) {
-        const uint32_t i = base + r * 32 + lane;
-        const bool valid = i < n;
-        uint32_t d = kBins;  // sentinel for lanes past the end
-        if (valid) d = ((FIRST ? first_key(keys, i) : keys[i]) >> shift) & (kBins - 1);
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (valid && lane == (unsigned)(__ffs(peers) - 1)) s_cnt[warp][d] += __popc(peers);
+        for (int r = 0; r < kRounds; ++r) {
+            const uint32_t i = base + r * 32 + lane;
+            const bool valid = i < n;
+            uint32_t d = kBins;  // sentinel for lanes past the end
+            if (valid) {
+                uint32_t key, val;
+                load_key<SRC>(cnt, keys_in, vals_in, i, key, val);
+                d = (key >> shift) & (kBins - 1);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == (unsigned)(__ffs(peers) - 1)) s_cnt[warp][d] += __popc(peers);
+        }
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kBins; d += kSortBlock) {
@@ -147,16 +200,20 @@ cudaError_t exclusive_scan(uint32_t *d_data, uint32_t L, uint32_t *d_block_sums,
 }
 
 // ------------------------------------------------------------------ downsweep
-template <bool FIRST, bool LAST>
+template <int SRC, int OUT>
 __global__ void __launch_bounds__(kSortBlock)
-    k_radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t n,
-                      int shift, const uint32_t *__restrict__ tile_off, uint32_t num_tiles,
-                      uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int32_t *__restrict__ rank_out) {
+    k_radix_downsweep(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ keys_in,
+                      const uint32_t *__restrict__ vals_in, uint32_t n_host, const uint32_t *__restrict__ n_dev,
+                      uint32_t n_all, int shift, const uint32_t *__restrict__ tile_off, uint32_t num_tiles,
+                      uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, uint32_t *__restrict__ perm,
+                      int32_t *__restrict__ rank_out) {
     __shared__ uint32_t s_cnt[kWarps][kBins];
     __shared__ uint32_t s_base[kBins];
+    const uint32_t n = n_dev ? *n_dev : n_host;
+    const uint32_t tile = blockIdx.x;
+    if (tile * kTile >= n) return;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     for (int i = threadIdx.x; i < kWarps * kBins; i += kSortBlock) (&s_cnt[0][0])[i] = 0;
-    const uint32_t tile = blockIdx.x;
     for (int d = threadIdx.x; d < kBins; d += kSortBlock) s_base[d] = tile_off[(size_t)d * num_tiles + tile];
     __syncthreads();
 
@@ -167,11 +224,10 @@ __global__ void __launch_bounds__(kSortBlock)
         const uint32_t i = base + r * 32 + lane;
         const bool valid = i < n;
         key[r] = 0;
-        val[r] = i;
+        val[r] = 0;
         uint32_t d = kBins;
         if (valid) {
-            key[r] = FIRST ? first_key(keys_in, i) : keys_in[i];
-            if (!FIRST) val[r] = vals_in[i];
+            load_key<SRC>(cnt, keys_in, vals_in, i, key[r], val[r]);
             d = (key[r] >> shift) & (kBins - 1);
         }
         const unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -202,12 +258,14 @@ __global__ void __launch_bounds__(kSortBlock)
         if (i < n) {
             const uint32_t d = (key[r] >> shift) & (kBins - 1);
             const uint32_t pos = s_cnt[warp][d] + loc[r];
-            // pos < n and val < n hold when the scan is consistent; the checks keep a
+            // pos < n and val < n_all hold when the scan is consistent; the checks keep a
             // defect from ever turning into an out-of-bounds store
-            if (pos >= n || val[r] >= n) continue;
-            if (LAST) {
-                vals_out[pos] = val[r];
+            if (pos >= n || val[r] >= n_all) continue;
+            if (OUT == kOutFinal || (OUT == kOutSplit && d != 0)) {
+                perm[pos] = val[r];
                 rank_out[val[r]] = (int32_t)pos;
+            } else if (OUT == kOutSplit) {
+                vals_out[pos] = val[r];
             } else {
                 keys_out[pos] = key[r];
                 vals_out[pos] = val[r];
@@ -231,7 +289,7 @@ int key_bits(int64_t F) {
 
 struct SortLayout {
     uint32_t num_tiles, L, nblk;
-    size_t off_ka, off_va, off_kb, off_vb, off_hist, off_bsum, total;
+    size_t off_ka, off_va, off_kb, off_vb, off_hist, off_bsum, off_nh, total;
 };
 
 SortLayout sort_layout(int32_t N) {
@@ -247,6 +305,7 @@ SortLayout sort_layout(int32_t N) {
     s.off_vb = o; o = up(o + 4ull * N);
     s.off_hist = o; o = up(o + 4ull * s.L);
     s.off_bsum = o; o = up(o + 4ull * (s.nblk + 1));
+    s.off_nh = o; o = up(o + 4ull);
     s.total = o;
     return s;
 }
@@ -257,66 +316,110 @@ size_t sort_scratch_bytes(int32_t N, int64_t F) {
     (void)F;
     return N > 0 ? sort_layout(N).total : 0;
 }
+static_assert(sort_scratch_bound(1) == 2560 && sort_scratch_bound(1 << 20) == 17039872, "scratch bound formula");
+
+namespace {
+
+struct Bufs {
+    uint32_t *ka, *va, *kb, *vb, *hist, *bsum, *nh;
+};
+
+template <int SRC, int OUT>
+cudaError_t radix_pass(const uint32_t *cnt, const uint32_t *kin, const uint32_t *vin, uint32_t n_host,
+                       const uint32_t *n_dev, uint32_t n_all, uint32_t tiles, int shift, const Bufs &b,
+                       uint32_t *kout, uint32_t *vout, uint32_t *perm, int32_t *rank, cudaStream_t st) {
+    const uint32_t L = tiles * kBins;
+    k_radix_upsweep<SRC><<<tiles, kSortBlock, 0, st>>>(cnt, kin, vin, n_host, n_dev, shift, b.hist, tiles);
+    cudaError_t e = exclusive_scan(b.hist, L, b.bsum, st);
+    if (e != cudaSuccess) return e;
+    k_radix_downsweep<SRC, OUT><<<tiles, kSortBlock, 0, st>>>(cnt, kin, vin, n_host, n_dev, n_all, shift, b.hist,
+                                                              tiles, kout, vout, perm, rank);
+    note_launches(2);  // upsweep + downsweep
+    return cudaGetLastError();
+}
+
+// LSD passes over key bits [0, bits): first pass from SRC_FIRST, last writes perm/rank.
+template <int SRC_FIRST>
+cudaError_t lsd_sort(const uint32_t *cnt, const uint32_t *ids, uint32_t n_host, const uint32_t *n_dev,
+                     uint32_t n_all, uint32_t tiles, int bits, const Bufs &b, uint32_t *perm, int32_t *rank,
+                     cudaStream_t st) {
+    const int passes = (bits + kBits - 1) / kBits;
+    const uint32_t *kin = nullptr, *vin = ids;
+    uint32_t *kout = b.ka, *vout = b.va;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * kBits;
+        const bool first = p == 0, last = p == passes - 1;
+        cudaError_t e;
+        if (first && last)
+            e = radix_pass<SRC_FIRST, kOutFinal>(cnt, kin, vin, n_host, n_dev, n_all, tiles, shift, b, nullptr,
+                                                 nullptr, perm, rank, st);
+        else if (first)
+            e = radix_pass<SRC_FIRST, kOutPairs>(cnt, kin, vin, n_host, n_dev, n_all, tiles, shift, b, kout, vout,
+                                                 nullptr, nullptr, st);
+        else if (last)
+            e = radix_pass<kSrcPairs, kOutFinal>(cnt, kin, vin, n_host, n_dev, n_all, tiles, shift, b, nullptr,
+                                                 nullptr, perm, rank, st);
+        else
+            e = radix_pass<kSrcPairs, kOutPairs>(cnt, kin, vin, n_host, n_dev, n_all, tiles, shift, b, kout, vout,
+                                                 nullptr, nullptr, st);
+        if (e != cudaSuccess) return e;
+        kin = kout;
+        vin = vout;
+        if (kout == b.ka) {
+            kout = b.kb;
+            vout = b.vb;
+        } else {
+            kout = b.ka;
+            vout = b.va;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
 
 cudaError_t launch_sort_by_count(const uint32_t *d_cnt, int32_t N, int64_t F, int32_t *d_perm, int32_t *d_rank,
                                  void *d_scratch, size_t scratch_bytes, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     const int bits = key_bits(F);
-    const int passes = (bits + kBits - 1) / kBits;
-    if (passes == 0) {
+    if (bits == 0) {  // F == 0: every count is 0, the order is the identity
         const int sms = device_sm_count();
         k_identity_perm<<<sms * 4, 256, 0, st>>>(d_perm, d_rank, N);
         note_launches(1);
         return cudaGetLastError();
     }
     const SortLayout s = sort_layout(N);
+    if (s.total != sort_scratch_bound(size_t(N))) return cudaErrorInvalidValue;  // layout and bound agree
     if (scratch_bytes < s.total || d_scratch == nullptr) return cudaErrorInvalidValue;
     char *w = static_cast<char *>(d_scratch);
-    uint32_t *ka = reinterpret_cast<uint32_t *>(w + s.off_ka), *va = reinterpret_cast<uint32_t *>(w + s.off_va);
-    uint32_t *kb = reinterpret_cast<uint32_t *>(w + s.off_kb), *vb = reinterpret_cast<uint32_t *>(w + s.off_vb);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(w + s.off_hist);
-    uint32_t *bsum = reinterpret_cast<uint32_t *>(w + s.off_bsum);
+    Bufs b;
+    b.ka = reinterpret_cast<uint32_t *>(w + s.off_ka);
+    b.va = reinterpret_cast<uint32_t *>(w + s.off_va);
+    b.kb = reinterpret_cast<uint32_t *>(w + s.off_kb);
+    b.vb = reinterpret_cast<uint32_t *>(w + s.off_vb);
+    b.hist = reinterpret_cast<uint32_t *>(w + s.off_hist);
+    b.bsum = reinterpret_cast<uint32_t *>(w + s.off_bsum);
+    b.nh = reinterpret_cast<uint32_t *>(w + s.off_nh);
     const uint32_t n = (uint32_t)N;
+    uint32_t *perm = reinterpret_cast<uint32_t *>(d_perm);
 
-    const uint32_t *kin = d_cnt, *vin = nullptr;
-    uint32_t *kout = ka, *vout = va;
-    for (int p = 0; p < passes; ++p) {
-        const int shift = p * kBits;
-        const bool first = p == 0, last = p == passes - 1;
-        if (first)
-            k_radix_upsweep<true><<<s.num_tiles, kSortBlock, 0, st>>>(kin, n, shift, hist, s.num_tiles);
-        else
-            k_radix_upsweep<false><<<s.num_tiles, kSortBlock, 0, st>>>(kin, n, shift, hist, s.num_tiles);
-        cudaError_t e = exclusive_scan(hist, s.L, bsum, st);
-        if (e != cudaSuccess) return e;
-        uint32_t *perm_u = reinterpret_cast<uint32_t *>(d_perm);
-        if (first && last)
-            k_radix_downsweep<true, true><<<s.num_tiles, kSortBlock, 0, st>>>(kin, vin, n, shift, hist, s.num_tiles,
-                                                                              nullptr, perm_u, d_rank);
-        else if (first)
-            k_radix_downsweep<true, false><<<s.num_tiles, kSortBlock, 0, st>>>(kin, vin, n, shift, hist, s.num_tiles,
-                                                                               kout, vout, nullptr);
-        else if (last)
-            k_radix_downsweep<false, true><<<s.num_tiles, kSortBlock, 0, st>>>(kin, vin, n, shift, hist, s.num_tiles,
-                                                                               nullptr, perm_u, d_rank);
-        else
-            k_radix_downsweep<false, false><<<s.num_tiles, kSortBlock, 0, st>>>(kin, vin, n, shift, hist,
-                                                                                s.num_tiles, kout, vout, nullptr);
-        note_launches(2);  // upsweep + downsweep
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        // ping-pong
-        kin = kout;
-        vin = vout;
-        if (kout == ka) {
-            kout = kb;
-            vout = vb;
-        } else {
-            kout = ka;
-            vout = va;
-        }
-    }
-    return cudaSuccess;
+    // heavy/light split when counts are mostly small and more than one pass is needed
+    const bool split = bits > kBits && F <= int64_t(64) * N;
+    if (!split) return lsd_sort<kSrcCounts>(d_cnt, nullptr, n, nullptr, n, s.num_tiles, bits, b, perm, d_rank, st);
+
+    // pass A: light ids final, heavy ids (digit 0) collected at the front of vb
+    cudaError_t e = radix_pass<kSrcClamped, kOutSplit>(d_cnt, nullptr, nullptr, n, nullptr, n, s.num_tiles, 0, b,
+                                                       nullptr, b.vb, perm, d_rank, st);
+    if (e != cudaSuccess) return e;
+    // H = number of heavy ids = scanned offset of (digit 1, tile 0)
+    e = cudaMemcpyAsync(b.nh, b.hist + s.num_tiles, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    // heavy ids: at most F / 255 of them
+    const int64_t hmax = std::min<int64_t>(N, F / 255 + 1);
+    const uint32_t htiles = (uint32_t)((hmax + kTile - 1) / kTile);
+    // the heavy ids move from vb into ka/va and back, so pass them in a buffer the
+    // ping-pong does not write first: copy to vb is the input, lsd writes ka/va first
+    return lsd_sort<kSrcGather>(d_cnt, b.vb, 0, b.nh, n, htiles, bits, b, perm, d_rank, st);
 }
 
 }  // namespace skx

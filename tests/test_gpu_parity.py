@@ -93,6 +93,28 @@ def test_build_index_unaligned(offset):
     assert np.array_equal(idx.counts.cpu().numpy().view(np.uint32).astype(np.uint64), cnt)
 
 
+def test_sort_heavy_light_split_cases():
+    """Counts >= 255 take the multi-pass path, smaller ones the single clamped pass."""
+    rng = np.random.default_rng(17)
+    cases = []
+    # heavy ties: ids 0..999 each exactly 300 times, plus a light tail over 50K ids
+    fk = np.concatenate([np.repeat(np.arange(1000, dtype=np.int32), 300),
+                         rng.integers(1000, 50_000, 600_000, dtype=np.int32)])
+    cases.append((fk[rng.permutation(fk.size)], 50_000))
+    # no heavy id at all (every count < 255), F/N <= 64
+    cases.append((rng.integers(0, 5000, 300_000, dtype=np.int32), 5000))
+    # one heavy id with a count above 2^24, everything else light
+    cases.append((np.concatenate([np.full(17_000_000, 7, dtype=np.int32),
+                                  rng.integers(0, 400_000, 1_000_000, dtype=np.int32)]), 400_000))
+    # F > 64 N: the plain multi-pass sort
+    cases.append((rng.integers(0, 1000, 200_000, dtype=np.int32), 1000))
+    for fk, n in cases:
+        idx = skx.skx_build_index(dev(fk), n)
+        cnt, perm, rank = oracle.build_index(fk, n)
+        assert np.array_equal(idx.perm.cpu().numpy(), perm)
+        assert np.array_equal(idx.rank.cpu().numpy(), rank)
+
+
 def test_build_index_all_same_key_and_ties():
     n = 5000
     fk = np.full(123_457, 4321, dtype=np.int32)
@@ -281,6 +303,46 @@ def test_probe_wraparound_and_negative():
         for t in (skx.Tuning.plain(), None, _tuning(hot_keys=1, lane_keys=1)):
             got = skx.skx_probe_aggregate(dev(rows), dev(fk), dev(m), _q(d), tuning=t)
             assert np.array_equal(got.cpu().numpy(), want)
+
+
+# ------------------------------------------------------------------ query preprocessing copies
+@pytest.mark.parametrize("cols", [[0, 1, 2, 3], [2, 0], [5, 1, 0], [0]])
+def test_reorder_columns_parity(probe_data, cols):
+    n = probe_data["dim"].shape[0]
+    idx = skx.skx_build_index(probe_data["d_fk"], n)
+    _, perm, _ = oracle.build_index(probe_data["fk"], n)
+    want = oracle.reorder(perm, np.ascontiguousarray(probe_data["dim"][:, cols]))
+    got = skx.skx_reorder_columns(idx, probe_data["d_dim"], cols)
+    assert np.array_equal(got.cpu().numpy(), want)
+    plain = skx.skx_reorder_columns(None, probe_data["d_dim"], cols)
+    assert np.array_equal(plain.cpu().numpy(), probe_data["dim"][:, cols])
+
+
+@pytest.mark.parametrize("qname", ["groupby", "sum", "count", "groupby_nofilter_payload1", "sum_payload3"])
+def test_query_copy_end_to_end(probe_data, qname):
+    """Probe over the 8-byte prefiltered copy == oracle on the original layout."""
+    d = QUERIES[qname]
+    want = _oracle(probe_data["dim"], probe_data["fk"], probe_data["m"], d)
+    q = _q(d)
+    qp = skx.skx_query_prefiltered(q)
+    n = probe_data["dim"].shape[0]
+    idx = skx.skx_build_index(probe_data["d_fk"], n)
+    fk2 = torch.empty_like(probe_data["d_fk"])
+    skx.skx_remap(idx, probe_data["d_fk"], fk2)
+    for index, keys in [(idx, fk2), (None, probe_data["d_fk"])]:
+        rows8 = skx.skx_reorder_query(index, probe_data["d_dim"], q)
+        for t in (None, skx.Tuning.plain(), _tuning(hot_keys=2048, lane_keys=16)):
+            got = skx.skx_probe_aggregate(rows8, keys, probe_data["d_m"], qp, tuning=t)
+            assert np.array_equal(got.cpu().numpy(), want), (qname, t)
+    # the copy itself, element by element
+    _, perm, _ = oracle.build_index(probe_data["fk"], n)
+    src = oracle.reorder(perm, probe_data["dim"])
+    passes = src[:, d["filter_col"]] < d["filter_lt"] if d["filter_col"] >= 0 else np.ones(n, bool)
+    key = (src[:, d["group_col"]] if d["agg"] == oracle.AGG_GROUPBY_SUM else np.zeros(n, np.int32))
+    key = np.where(passes, key, qp.num_groups)
+    pay = src[:, d["payload_col"]] if (d["payload_col"] >= 0 and d["agg"] != oracle.AGG_COUNT) else np.ones(n, np.int32)
+    got = skx.skx_reorder_query(idx, probe_data["d_dim"], q).cpu().numpy()
+    assert np.array_equal(got[:, 0], key) and np.array_equal(got[:, 1], pay)
 
 
 # ------------------------------------------------------------------ errors
