@@ -151,6 +151,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Max of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ====================================================================== ours
 def run_ours(a, rank, world, local_rank):
     import torch
@@ -230,11 +240,7 @@ def run_ours(a, rank, world, local_rank):
         idx.close()
     step_ms = [e[0].elapsed_time(e[5]) for e in evs]
     stage_ms = {s: [e[i].elapsed_time(e[i + 1]) for e in evs] for i, s in enumerate(stages)}
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     result = out.cpu().numpy().copy()
 
     # ---------------- the same path with the query-specific 8-byte copy (Section III-B)
@@ -410,11 +416,7 @@ def run_ours(a, rank, world, local_rank):
             t0 = time.perf_counter()
             skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
             t.append(time.perf_counter() - t0)
-        e2e_s = sum(t)
-        if dist is not None:
-            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(sum(t), dist, dev)
         e2e = {"value": round(world * a.f * n_e2e / e2e_s / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": int(h_dim.numel() * 4 + 2 * a.f * 4), "d2h_bytes_per_step": 8 * 1000,
                "ms_per_step": round(1e3 * e2e_s / n_e2e, 3), "steps": n_e2e,
