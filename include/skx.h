@@ -263,6 +263,49 @@ skx_status skx_probe_autotune(const void *d_rows, int32_t N, int32_t row_bytes, 
                               int64_t *d_out, void *stream, skx_tuning *out, float *best_ms);
 
 /* ------------------------------------------------------------------------
+ * Batched probes (many queries, one persistent launch).  Each descriptor is
+ * one skx_probe_aggregate call against the same dimension table: remapped
+ * keys fk[F] and measures (device), the query, and a device output of
+ * num_groups (GROUPBY_SUM, at most 4096 in a batch) or 1 int64.  The fact
+ * rows of all queries are cut into tiles that a persistent grid pulls from
+ * one atomic counter, so uneven batch sizes balance across the SMs; a small
+ * prologue kernel clears every output first.  Results equal the single-call
+ * results bit for bit.  The paper processes one query at a time; batching is
+ * this library's systems extension of the same operator (Sections IV-A, IV-B).
+ * ------------------------------------------------------------------------ */
+typedef struct skx_probe_desc {
+    const int32_t *fk;      /* device, F keys (remapped layout: frequency ranks) */
+    const int32_t *measure; /* device, F measures; may be NULL for COUNT */
+    int64_t F;
+    skx_query q;
+    int64_t *out;           /* device, num_groups or 1 entries, fully overwritten */
+} skx_probe_desc;
+
+typedef struct skx_batch_plan skx_batch_plan; /* opaque: descriptors and tile table on the device */
+
+/* Uploads the n descriptors (copied; the host array may be reused after the
+ * call) and builds the tile table (tile_rows fact rows per tile, 0 = 65536).
+ * tuning as for skx_probe_aggregate (hot_keys 0 = 1024 here).  Synchronises
+ * `stream` once.  Errors: SKX_EINVAL, SKX_ENOTSUP (more than 4096 groups),
+ * SKX_ENOMEM, SKX_ECUDA. */
+skx_status skx_batch_plan_create(const void *d_rows, int32_t N, int32_t row_bytes, const skx_probe_desc *h_descs,
+                                 int32_t n, const skx_tuning *tuning, int32_t tile_rows, void *stream,
+                                 skx_batch_plan **out);
+/* Enqueues the batch on `stream` (2 kernels).  use_graph != 0: the two
+ * launches are captured once into a CUDA graph (on first use) and the graph
+ * is replayed on `stream`. */
+skx_status skx_batch_plan_launch(skx_batch_plan *plan, int use_graph, void *stream);
+/* Times candidate tile sizes, launch shapes and hot-prefix sizes on the
+ * plan's own data (synchronously, outputs used as scratch) and keeps the
+ * fastest; returns it in *out, *tile_rows_out, *best_ms (each may be NULL). */
+skx_status skx_batch_plan_autotune(skx_batch_plan *plan, void *stream, skx_tuning *out, int32_t *tile_rows_out,
+                                   float *best_ms);
+void skx_batch_plan_destroy(skx_batch_plan *plan);
+/* One-shot: create, launch, synchronise, destroy. */
+skx_status skx_probe_batch(const void *d_rows, int32_t N, int32_t row_bytes, const skx_probe_desc *h_descs,
+                           int32_t n, const skx_tuning *tuning, void *stream);
+
+/* ------------------------------------------------------------------------
  * Whole path from host memory (Sections III-A, III-B and IV in sequence):
  * copies h_fk[F], h_measure[F] and the dimension table h_rows[N * row_bytes]
  * to the device, builds the index, remaps the keys, reorders the rows,

@@ -65,6 +65,11 @@ class Query(ctypes.Structure):
                 f"group_col={self.group_col}, num_groups={self.num_groups}, payload_col={self.payload_col})")
 
 
+class ProbeDesc(ctypes.Structure):
+    _fields_ = [("fk", ctypes.c_void_p), ("measure", ctypes.c_void_p), ("F", ctypes.c_int64), ("q", Query),
+                ("out", ctypes.c_void_p)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("hot_keys", ctypes.c_int32),
                 ("lane_keys", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32), ("unroll", ctypes.c_int32),
@@ -128,6 +133,16 @@ def lib():
             L.skx_probe_autotune.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), ctypes.c_int, P, P,
                                              ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_float)]
             L.skx_probe_autotune.restype = st
+            L.skx_batch_plan_create.argtypes = [P, i32, i32, ctypes.POINTER(ProbeDesc), i32, ctypes.POINTER(Tuning), i32,
+                                                P, ctypes.POINTER(P)]
+            L.skx_batch_plan_create.restype = st
+            L.skx_batch_plan_launch.argtypes = [P, ctypes.c_int, P]; L.skx_batch_plan_launch.restype = st
+            L.skx_batch_plan_autotune.argtypes = [P, P, ctypes.POINTER(Tuning), ctypes.POINTER(i32),
+                                                  ctypes.POINTER(ctypes.c_float)]
+            L.skx_batch_plan_autotune.restype = st
+            L.skx_batch_plan_destroy.argtypes = [P]; L.skx_batch_plan_destroy.restype = None
+            L.skx_probe_batch.argtypes = [P, i32, i32, ctypes.POINTER(ProbeDesc), i32, ctypes.POINTER(Tuning), P]
+            L.skx_probe_batch.restype = st
             L.skx_join_aggregate_host.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), P, P]
             L.skx_join_aggregate_host.restype = st
             _lib = L
@@ -355,6 +370,59 @@ def skx_probe_autotune(rows, fk, measure, query: Query, remapped: bool = True, o
                                     fk.numel(), ctypes.byref(query), int(remapped), _dptr(out, "out", torch.int64),
                                     _stream(stream), ctypes.byref(t), ctypes.byref(ms)), "skx_probe_autotune")
     return t, ms.value
+
+
+def _descs(items):
+    """items: iterable of (fk, measure_or_None, Query, out) with CUDA tensors -> ctypes array."""
+    import torch
+    items = list(items)
+    arr = (ProbeDesc * len(items))()
+    for i, (fk, m, q, out) in enumerate(items):
+        if out.numel() < q.nout:
+            raise ValueError("output too small for the query")
+        arr[i] = ProbeDesc(_dptr(fk, "fk", torch.int32), _dptr(m, "measure", torch.int32) if m is not None else None,
+                           fk.numel(), q, _dptr(out, "out", torch.int64))
+    return arr
+
+
+class BatchPlan:
+    """Many probes against one dimension table in one persistent launch (optionally a CUDA graph)."""
+
+    def __init__(self, rows, items, tuning: Tuning | None = None, tile_rows: int = 0, stream=None):
+        self._keep = list(items)  # the tensors must outlive the plan
+        arr = _descs(self._keep)
+        self._h = ctypes.c_void_p()
+        _check(lib().skx_batch_plan_create(_dptr(rows, "rows"), rows.shape[0], _row_bytes(rows), arr, len(arr),
+                                           ctypes.byref(tuning) if tuning is not None else None, int(tile_rows),
+                                           _stream(stream), ctypes.byref(self._h)), "skx_batch_plan_create")
+        self.rows = rows
+
+    def launch(self, use_graph: bool = False, stream=None):
+        _check(lib().skx_batch_plan_launch(self._h, int(use_graph), _stream(stream)), "skx_batch_plan_launch")
+
+    def autotune(self, stream=None):
+        t, tile, ms = Tuning(), ctypes.c_int32(), ctypes.c_float()
+        _check(lib().skx_batch_plan_autotune(self._h, _stream(stream), ctypes.byref(t), ctypes.byref(tile),
+                                             ctypes.byref(ms)), "skx_batch_plan_autotune")
+        return t, tile.value, ms.value
+
+    def close(self):
+        if self._h:
+            lib().skx_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def skx_probe_batch(rows, items, tuning: Tuning | None = None, stream=None):
+    arr = _descs(items)
+    _check(lib().skx_probe_batch(_dptr(rows, "rows"), rows.shape[0], _row_bytes(rows), arr, len(arr),
+                                 ctypes.byref(tuning) if tuning is not None else None, _stream(stream)),
+           "skx_probe_batch")
 
 
 def skx_join_aggregate_host(rows, fk, measure, query: Query, out=None, stream=None):

@@ -26,8 +26,8 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 LIBS = {
     "libskx.so": {
         "dir": os.path.join(PKG, "csrc"),
-        "sources": ["api.cu", "histogram.cu", "sort.cu", "remap.cu", "probe.cu", "autotune.cu", "noalloc.cu"],
-        "headers": ["skx_internal.cuh", os.path.join(INCLUDE, "skx.h")],
+        "sources": ["api.cu", "histogram.cu", "sort.cu", "remap.cu", "probe.cu", "autotune.cu", "batch.cu", "noalloc.cu"],
+        "headers": ["skx_internal.cuh", "probe_core.cuh", os.path.join(INCLUDE, "skx.h")],
     },
     "libskx_synth.so": {
         "dir": os.path.join(PKG, "synth"),

@@ -1,0 +1,145 @@
+// probe_core.cuh -- per-row logic of the FK-join probe, shared by the single
+// probe (probe.cu) and the batched persistent probe (batch.cu): the gather of
+// the needed dimension columns, the filter, the group/SUM/COUNT fold and the
+// exact 32-bit hot-key sums of threshold-based processing (Section IV-B).
+#pragma once
+
+#include "skx_internal.cuh"
+
+namespace skx {
+namespace pcore {
+
+constexpr int kMaxSmemGroups = 4096;
+
+struct PP {
+    const int32_t *fk, *measure;
+    int64_t F, head;
+    const char *rows;
+    int32_t N, row_bytes;
+    int32_t fcol, flt, gcol, G, pcol;
+    int32_t t_hot, t_lane;
+    int32_t gather_policy;
+    unsigned long long *out;
+    unsigned *err;
+};
+
+__device__ __forceinline__ int sel4(const int4 &v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ int2 ld_gather8(const int2 *p, uint64_t pol) {
+    int2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.s32 {%0,%1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ int sel2(const int2 &v, int c) { return c == 0 ? v.x : v.y; }
+
+// Row access paths: 16-byte rows (or wider, columns in the first 16 bytes),
+// 8-byte rows, or one 4-byte load per needed column.
+enum RowPath { kRowGeneric = 0, kRow16 = 1, kRow8 = 2 };
+
+// Gathered values of one dimension row: x = filter column, y = group column, z = payload.
+template <int PATH, int AGG>
+__device__ __forceinline__ int4 fetch_row(const PP &p, int32_t k, uint64_t pol) {
+    const char *r = p.rows + size_t(k) * size_t(p.row_bytes);
+    int4 v;
+    if (PATH == kRow8) {
+        const int2 raw = ld_gather8(reinterpret_cast<const int2 *>(r), pol);
+        v.x = p.fcol >= 0 ? sel2(raw, p.fcol) : 0;
+        v.y = AGG == SKX_AGG_GROUPBY_SUM ? sel2(raw, p.gcol) : 0;
+        v.z = p.pcol >= 0 ? sel2(raw, p.pcol) : 1;
+    } else if (PATH == kRow16) {
+        const int4 raw = ld_gather16(reinterpret_cast<const int4 *>(r), pol);
+        v.x = p.fcol >= 0 ? sel4(raw, p.fcol) : 0;
+        v.y = AGG == SKX_AGG_GROUPBY_SUM ? sel4(raw, p.gcol) : 0;
+        v.z = p.pcol >= 0 ? sel4(raw, p.pcol) : 1;
+    } else {
+        const int *ri = reinterpret_cast<const int *>(r);
+        v.x = p.fcol >= 0 ? ld_gather4(ri + p.fcol, pol) : 0;
+        v.y = AGG == SKX_AGG_GROUPBY_SUM ? ld_gather4(ri + p.gcol, pol) : 0;
+        v.z = (AGG != SKX_AGG_COUNT && p.pcol >= 0) ? ld_gather4(ri + p.pcol, pol) : 1;
+    }
+    v.w = 0;
+    return v;
+}
+
+__device__ __forceinline__ bool passes(const PP &p, const int4 &v) { return p.fcol < 0 || v.x < p.flt; }
+
+// Fold `amount` (a measure, a hot-key measure sum, or a count) for a row whose
+// gathered values are v.
+template <int AGG, bool GSMEM>
+__device__ __forceinline__ void fold(const PP &p, const int4 &v, unsigned long long amount, unsigned long long &acc,
+                                     unsigned long long *s_grp) {
+    if (!passes(p, v)) return;
+    if (AGG == SKX_AGG_COUNT) {
+        acc += amount;
+        return;
+    }
+    const unsigned long long prod = amount * (unsigned long long)(long long)v.z;
+    if (AGG == SKX_AGG_SUM) {
+        acc += prod;
+        return;
+    }
+    if ((uint32_t)v.y < (uint32_t)p.G) {
+        if (GSMEM)
+            atomicAdd(s_grp + v.y, prod);
+        else
+            atomicAdd(p.out + v.y, prod);
+    } else {
+        raise_error(p.err, kErrGroupRange);
+    }
+}
+
+// Hot-key sums are kept exactly in two 32-bit shared words (32-bit shared
+// atomics run about 4x faster than 64-bit ones on this part): lo accumulates
+// the measures as unsigned 32-bit values, hi counts the wrap-arounds of lo
+// minus the number of negative measures.  Then sum = lo + 2^32 * hi exactly,
+// because a measure m < 0 enters lo as m + 2^32.
+struct HotRef {
+    uint32_t *lo;
+    int32_t *hi;
+};
+
+template <int AGG>
+__device__ __forceinline__ void hot_add(HotRef h, int32_t m) {
+    if (AGG == SKX_AGG_COUNT) {
+        atomicAdd(h.lo, 1u);  // a CTA sees fewer than 2^32 rows
+        return;
+    }
+    const uint32_t u = (uint32_t)m;
+    const uint32_t old = atomicAdd(h.lo, u);
+    const int d = (int)(old + u < old) - (int)(m < 0);
+    if (d) atomicAdd(h.hi, d);
+}
+
+__device__ __forceinline__ unsigned long long hot_value(uint32_t lo, int32_t hi) {
+    return (unsigned long long)lo + ((unsigned long long)(long long)hi << 32);
+}
+
+struct HotArrays {
+    uint32_t *lo, *lane_lo;
+    int32_t *hi, *lane_hi;
+};
+
+template <int AGG, int PATH, bool GSMEM>
+__device__ __forceinline__ void handle(const PP &p, int32_t k, int32_t m, const int4 &row, unsigned long long &acc,
+                                       unsigned long long *s_grp, const HotArrays &h, unsigned lane) {
+    if ((uint32_t)k < (uint32_t)p.t_hot) {
+        if ((uint32_t)k < (uint32_t)p.t_lane) {
+            const size_t i = (size_t(k) << 5) + lane;
+            hot_add<AGG>(HotRef{h.lane_lo + i, h.lane_hi + i}, m);
+        } else {
+            hot_add<AGG>(HotRef{h.lo + k, h.hi + k}, m);
+        }
+    } else if ((uint32_t)k < (uint32_t)p.N) {
+        const unsigned long long amount = AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)m;
+        fold<AGG, GSMEM>(p, row, amount, acc, s_grp);
+    } else {
+        raise_error(p.err, kErrKeyRange);
+    }
+}
+
+
+}  // namespace pcore
+}  // namespace skx

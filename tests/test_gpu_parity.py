@@ -345,6 +345,80 @@ def test_query_copy_end_to_end(probe_data, qname):
     assert np.array_equal(got[:, 0], key) and np.array_equal(got[:, 1], pay)
 
 
+# ------------------------------------------------------------------ batched probes
+@pytest.fixture(scope="module")
+def batch_data():
+    n = 200_000
+    w = synth.Workload(n, 2_000_000, 1.0, seed=31, width=16)
+    fk_all, m_all, dim = w.fk(), w.measure(), w.dim()
+    cnt, perm, rank = oracle.build_index(fk_all, n)
+    rng = np.random.default_rng(5)
+    qs = []
+    kinds = [QUERIES["groupby"], QUERIES["sum"], QUERIES["count"], QUERIES["groupby_nofilter_payload1"],
+             QUERIES["sum_payload3"], dict(QUERIES["groupby"], num_groups=4096),
+             dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=1, filter_lt=90, group_col=1, num_groups=100, payload_col=3)]
+    sizes = [0, 1, 3, 4, 5, 17, 1000, 4099, 65536, 65537, 250_001, 2_000_000]
+    for i in range(40):
+        f = sizes[i % len(sizes)] if i < len(sizes) else int(rng.integers(1, 300_000))
+        start = int(rng.integers(0, fk_all.size - f + 1))
+        d = kinds[i % len(kinds)]
+        qs.append((start, f, d, int(rng.integers(0, 4)) if i % 5 == 0 else 0))
+    return dict(n=n, fk=fk_all, m=m_all, dim=dim, rank=rank, perm=perm, qs=qs,
+                d_dim2=dev(oracle.reorder(perm, dim)), fk2=oracle.remap(rank, fk_all))
+
+
+def _batch_items(bd):
+    items, wants = [], []
+    for start, f, d, off in bd["qs"]:
+        fk2 = bd["fk2"][start:start + f]
+        m = bd["m"][start:start + f]
+        d_fk = offset_view(fk2, off) if off else dev(fk2)
+        d_m = offset_view(m, off) if off else dev(m)
+        q = _q(d)
+        out = torch.full((q.nout,), -1, dtype=torch.int64, device=DEV)
+        items.append((d_fk, None if d["agg"] == oracle.AGG_COUNT else d_m, q, out))
+        wants.append(_oracle(bd["dim"], bd["fk"][start:start + f], m, d))
+    return items, wants
+
+
+def test_probe_batch_parity(batch_data):
+    items, wants = _batch_items(batch_data)
+    skx.skx_probe_batch(batch_data["d_dim2"], items)
+    for (_, _, _, out), want in zip(items, wants):
+        assert np.array_equal(out.cpu().numpy(), want)
+    assert status() == skx.SKX_OK
+
+
+def test_batch_plan_graph_replay_and_autotune(batch_data):
+    items, wants = _batch_items(batch_data)
+    plan = skx.BatchPlan(batch_data["d_dim2"], items, tile_rows=4096)
+    for use_graph in (False, True, True):
+        for _, _, _, out in items:
+            out.fill_(-1)
+        plan.launch(use_graph=use_graph)
+        torch.cuda.synchronize()
+        for (_, _, _, out), want in zip(items, wants):
+            assert np.array_equal(out.cpu().numpy(), want)
+    t, tile, ms = plan.autotune()
+    assert ms > 0 and tile > 0
+    for _, _, _, out in items:
+        out.fill_(-1)
+    plan.launch(use_graph=True)
+    torch.cuda.synchronize()
+    for (_, _, _, out), want in zip(items, wants):
+        assert np.array_equal(out.cpu().numpy(), want)
+    plan.close()
+    assert status() == skx.SKX_OK
+
+
+def test_batch_rejects_too_many_groups(batch_data):
+    fk = dev(batch_data["fk2"][:100])
+    out = torch.empty(5000, dtype=torch.int64, device=DEV)
+    with pytest.raises(skx.SkxError) as e:
+        skx.skx_probe_batch(batch_data["d_dim2"], [(fk, fk, skx.Query.groupby_sum(num_groups=5000), out)])
+    assert e.value.status == skx.SKX_ENOTSUP
+
+
 # ------------------------------------------------------------------ errors
 def test_key_and_group_range_errors():
     status()  # clear
