@@ -51,6 +51,9 @@ def parse_args():
     p.add_argument("--sweep-steps", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--batch-queries", type=int, default=512, help="queries of the batched workload (0 = skip)")
+    p.add_argument("--serve-n", type=int, default=50_000_000, help="rows of the served dimension table (0 = skip)")
+    p.add_argument("--serve-pool", type=int, default=256, help="distinct requests in the serving pool")
+    p.add_argument("--serve-requests", type=int, default=512, help="requests per arrival rate")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=0, help="fact rows in the oracle's timed sample (0 = all F)")
     p.add_argument("--ref-rows", type=int, default=4_000_000, help="fact rows per reference-arm step")
@@ -401,6 +404,12 @@ def run_ours(a, rank, world, local_rank):
         batch = run_batch(a, w, dev, stream, flush)
         torch.cuda.empty_cache()
 
+    # ---------------- serving: continuous batching over a resident 50M-row table
+    serving = None
+    if a.serve_n > 0 and rank == 0:
+        serving = run_serving(a, dev)
+        torch.cuda.empty_cache()
+
     # ---------------- end to end through the host-buffer C-ABI call
     e2e = None
     if not a.no_e2e:
@@ -452,7 +461,7 @@ def run_ours(a, rank, world, local_rank):
         "probe": {"remapped_p50_ms": round(statistics.median(probe_lat), 4) if probe_lat else None,
                   "remapped_p99_ms": round(float(np.percentile(probe_lat, 99)), 4) if probe_lat else None,
                   "sweep": sweep},
-        "batch": batch,
+        "batch": batch, "serving": serving,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
     }
     return line
@@ -539,6 +548,95 @@ def run_batch(a, w, dev, stream, flush):
             "speedup_vs_unbatched": round(t_single / t_graph, 3), "results_identical": bool(same),
             "tile_rows": tile, "tuning": {k: tuning.as_dict()[k] for k in ("block_threads", "ctas_per_sm",
                                                                           "hot_keys", "lane_keys")}}
+
+
+def run_serving(a, dev):
+    """Poisson arrivals against a device-resident 50M x 64 B table and resident permutation;
+    continuous batching vs the unbatched one-request-at-a-time path."""
+    import torch
+    import paper_1910_10063_gb300 as skx
+    from paper_1910_10063_gb300 import synth
+    n = a.serve_n
+    # the resident index: built from a seeded s = 1.0 sample of 25 N fact rows
+    ws = synth.DeviceWorkload(n, 25 * n, 1.0, seed=7, width=a.width, device=dev, with_measure=False)
+    idx = skx.skx_build_index(ws.fk, n)
+    dim2 = torch.empty_like(ws.dim)
+    skx.skx_reorder(idx, ws.dim, dim2)
+    rank = idx.rank.clone()
+    r2id = ws.r2id_host
+    del ws
+    idx.close()
+    torch.cuda.empty_cache()
+    # request pool: config-3 style fact batches (original keys) in pinned host memory
+    g = np.random.Generator(np.random.PCG64(synth.stream_key(11, 7)))
+    sizes = synth.lognormal_sizes(a.serve_pool, 11)
+    s_of = g.choice([0.8, 1.0, 1.2], size=a.serve_pool)
+    kind = g.integers(0, 3, size=a.serve_pool)
+    qdefs = [skx.Query.count(), skx.Query.sum(), skx.Query.groupby_sum()]
+    cdfs = {s: torch.from_numpy(synth.zipf_cdf(n, float(s))).to(dev) for s in (0.8, 1.0, 1.2)}
+    d_r2id = torch.from_numpy(r2id).to(dev)
+    pool = []
+    for i in range(a.serve_pool):
+        f = int(sizes[i])
+        fk = synth.zipf_fk_device(cdfs[float(s_of[i])], d_r2id, 5000 + i, f)
+        m = synth.measure_device(5000 + i, f, device=dev)
+        h_fk = torch.empty(f, dtype=torch.int32, pin_memory=True)
+        h_m = torch.empty(f, dtype=torch.int32, pin_memory=True)
+        h_fk.copy_(fk)
+        h_m.copy_(m)
+        pool.append((h_fk, h_m, qdefs[int(kind[i])]))
+    del cdfs, d_r2id
+    torch.cuda.empty_cache()
+    pool_rows = sum(int(x[0].numel()) for x in pool)
+
+    def run(srv, count, rate):
+        reqs = [srv.make_request(*pool[i % len(pool)]) for i in range(count)]
+        if rate is None:
+            arr = np.zeros(count)
+        else:
+            arr = np.cumsum(np.random.Generator(np.random.PCG64(99)).exponential(1.0 / rate, size=count))
+        t0 = time.perf_counter()
+        lat = srv.replay(reqs, arr, timeout_ms=600_000)
+        wall = time.perf_counter() - t0
+        rows = sum(int(pool[i % len(pool)][0].numel()) for i in range(count))
+        outs = [r[1][2] for r in reqs]
+        return lat, wall, rows, outs
+
+    def summary(lat, wall, rows, count, rate):
+        return {"offered_qps": None if rate is None else round(rate, 1), "achieved_qps": round(count / wall, 1),
+                "grows_s": round(rows / wall / 1e9, 2), "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3), "requests": count}
+
+    result = {"table": f"{n // 1_000_000}M x {a.width * 4}B resident rows + resident rank (index from a 25N-row "
+                       f"s=1.0 sample)", "pool_requests": len(pool), "pool_rows": pool_rows}
+    for mode, cfg in (("continuous_batching", skx.ServerConfig(max_inflight=64)),
+                      ("unbatched", skx.ServerConfig(max_inflight=1, round_rows=1 << 40))):
+        srv = skx.Server(dim2, rank, cfg)
+        run(srv, min(64, len(pool)), None)  # warm-up
+        lat, wall, rows, outs = run(srv, len(pool), None)  # saturation: everything at t = 0
+        cap = len(pool) / wall
+        entry = {"capacity_qps": round(cap, 1), "saturation": summary(lat, wall, rows, len(pool), None), "rates": []}
+        if mode == "continuous_batching":
+            ref_outs = outs
+            base_cap = cap
+        else:
+            if not all(np.array_equal(x, y) for x, y in zip(outs, ref_outs)):
+                raise RuntimeError("serving results differ between batched and unbatched modes")
+        for frac in (0.25, 0.5, 0.75, 0.9):
+            rate = frac * base_cap  # the same offered load for both modes
+            count = a.serve_requests
+            if mode == "unbatched" and rate > 1.5 * cap:
+                entry["rates"].append({"offered_qps": round(rate, 1), "skipped": "offered load above 1.5x capacity"})
+                continue
+            lat, wall, rows, _ = run(srv, count, rate)
+            entry["rates"].append(dict(summary(lat, wall, rows, count, rate), load_fraction=frac))
+        entry["stats"] = srv.stats()
+        srv.close()
+        result[mode] = entry
+    st = skx.skx_stream_status()
+    if st != skx.SKX_OK:
+        raise RuntimeError(f"device status {st} during serving")
+    return result
 
 
 def cpu_baseline(a, fk_host, m_host, dim_host, nthreads=None):

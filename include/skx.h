@@ -306,6 +306,67 @@ skx_status skx_probe_batch(const void *d_rows, int32_t N, int32_t row_bytes, con
                            int32_t n, const skx_tuning *tuning, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching over a resident index.
+ * The reordered dimension table (d_rows, skx_reorder output) and the index's
+ * rank array (old -> new, skx_index_rank) stay resident on the device and
+ * are borrowed for the server's lifetime.  Each request carries a fact batch
+ * with ORIGINAL keys in host memory (pinned memory copies fastest); the
+ * server copies it into a fixed device arena when an in-flight slot and
+ * arena room are free (admission by memory, arrival order), recodes the keys
+ * through the resident rank array (Section III-A), and runs the remaining
+ * rows of all admitted requests together in rounds of the batched probe, so
+ * requests arriving while others run join the next round and their copies
+ * overlap the running rounds.  Results are bit-identical to
+ * skx_probe_aggregate on the same data.  The paper has no serving layer;
+ * this is this library's systems extension.
+ * ------------------------------------------------------------------------ */
+typedef struct skx_server skx_server;
+
+typedef struct skx_server_config {
+    int32_t max_inflight;   /* requests admitted at once (device slots); default 64 */
+    int32_t tile_rows;      /* fact rows per batch tile; default 65536 */
+    int64_t round_rows;     /* fact rows per device round, over all requests; default 16 Mi */
+    int64_t memory_budget;  /* device arena for admitted requests, bytes; default min(free/2, 16 GiB) */
+    int32_t timeout_ms;     /* bound on any internal wait for the device; default 10000 */
+    int32_t reserved0;
+    skx_tuning tuning;      /* batch kernel tuning (hot_keys 0 = 1024) */
+    int32_t reserved[8];
+} skx_server_config;
+
+typedef struct skx_request {
+    const int32_t *h_fk;      /* host, F original keys in [0, N) */
+    const int32_t *h_measure; /* host, F measures (ignored for COUNT) */
+    int64_t F;
+    skx_query q;              /* GROUPBY_SUM: at most 4096 groups */
+    int64_t *h_out;           /* host, num_groups or 1 int64, written at completion */
+} skx_request;
+
+/* d_rank may be NULL when requests already carry remapped keys.  cfg may be
+ * NULL for defaults.  Starts the server thread. */
+skx_status skx_server_create(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_rank,
+                             const skx_server_config *cfg, skx_server **out);
+/* Queues a request (its host buffers must stay valid until it completes);
+ * returns at once with a ticket.  SKX_ENOMEM if it can never fit the arena. */
+skx_status skx_server_submit(skx_server *s, const skx_request *req, uint64_t *ticket);
+/* Waits up to timeout_ms for the request: SKX_OK (h_out written), the
+ * request's error, or SKX_ETIMEOUT. */
+skx_status skx_server_wait(skx_server *s, uint64_t ticket, int32_t timeout_ms);
+/* Host clock seconds (steady clock) of submit, admission and completion. */
+skx_status skx_server_request_times(skx_server *s, uint64_t ticket, double *submit_s, double *admit_s,
+                                    double *done_s);
+/* Forgets a finished ticket (SKX_EBUSY while it runs). */
+skx_status skx_server_release(skx_server *s, uint64_t ticket);
+/* Open-loop load generator: submits reqs[i] at arrival_s[i] seconds after
+ * the call starts (busy-waiting on the host clock), waits for all (bounded by
+ * timeout_ms overall) and writes each request's latency from its scheduled
+ * arrival to completion (-1 for a failed one) to latency_s[i]. */
+skx_status skx_server_replay(skx_server *s, const skx_request *reqs, const double *arrival_s, int32_t n,
+                             int32_t timeout_ms, double *latency_s);
+skx_status skx_server_stats(skx_server *s, uint64_t *rounds, uint64_t *rows, uint64_t *max_active);
+/* Finishes queued work, stops the thread and frees everything. */
+void skx_server_destroy(skx_server *s);
+
+/* ------------------------------------------------------------------------
  * Whole path from host memory (Sections III-A, III-B and IV in sequence):
  * copies h_fk[F], h_measure[F] and the dimension table h_rows[N * row_bytes]
  * to the device, builds the index, remaps the keys, reorders the rows,

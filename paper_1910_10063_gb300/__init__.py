@@ -90,6 +90,17 @@ class Tuning(ctypes.Structure):
         return f"Tuning({self.as_dict()})"
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("round_rows", ctypes.c_int64),
+                ("memory_budget", ctypes.c_int64), ("timeout_ms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("tuning", Tuning), ("reserved", ctypes.c_int32 * 8)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("h_fk", ctypes.c_void_p), ("h_measure", ctypes.c_void_p), ("F", ctypes.c_int64), ("q", Query),
+                ("h_out", ctypes.c_void_p)]
+
+
 def lib():
     """Load libskx.so (raises if it has not been built -- there is no fallback)."""
     global _lib
@@ -143,6 +154,22 @@ def lib():
             L.skx_batch_plan_destroy.argtypes = [P]; L.skx_batch_plan_destroy.restype = None
             L.skx_probe_batch.argtypes = [P, i32, i32, ctypes.POINTER(ProbeDesc), i32, ctypes.POINTER(Tuning), P]
             L.skx_probe_batch.restype = st
+            L.skx_server_create.argtypes = [P, i32, i32, P, ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
+            L.skx_server_create.restype = st
+            L.skx_server_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+            L.skx_server_submit.restype = st
+            L.skx_server_wait.argtypes = [P, ctypes.c_uint64, i32]; L.skx_server_wait.restype = st
+            L.skx_server_request_times.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+            L.skx_server_request_times.restype = st
+            L.skx_server_release.argtypes = [P, ctypes.c_uint64]; L.skx_server_release.restype = st
+            L.skx_server_replay.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double), i32, i32,
+                                            ctypes.POINTER(ctypes.c_double)]
+            L.skx_server_replay.restype = st
+            L.skx_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(ctypes.c_uint64)]
+            L.skx_server_stats.restype = st
+            L.skx_server_destroy.argtypes = [P]; L.skx_server_destroy.restype = None
             L.skx_join_aggregate_host.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), P, P]
             L.skx_join_aggregate_host.restype = st
             _lib = L
@@ -423,6 +450,84 @@ def skx_probe_batch(rows, items, tuning: Tuning | None = None, stream=None):
     _check(lib().skx_probe_batch(_dptr(rows, "rows"), rows.shape[0], _row_bytes(rows), arr, len(arr),
                                  ctypes.byref(tuning) if tuning is not None else None, _stream(stream)),
            "skx_probe_batch")
+
+
+class Server:
+    """Continuous-batching request loop over a resident reordered table and rank array.
+
+    Requests are (fk_host, measure_host_or_None, Query) with host numpy arrays or CPU tensors
+    holding ORIGINAL keys; results come back as int64 numpy arrays."""
+
+    def __init__(self, rows, rank=None, config: ServerConfig | None = None):
+        import torch
+        self._h = ctypes.c_void_p()
+        _check(lib().skx_server_create(_dptr(rows, "rows"), rows.shape[0], _row_bytes(rows),
+                                       _dptr(rank, "rank", torch.int32) if rank is not None else None,
+                                       ctypes.byref(config) if config is not None else None, ctypes.byref(self._h)),
+               "skx_server_create")
+        self.rows, self.rank = rows, rank
+        self._keep = {}
+
+    @staticmethod
+    def _host(a):
+        import numpy as np
+        import torch
+        if a is None:
+            return None, None
+        if isinstance(a, torch.Tensor):
+            return ctypes.c_void_p(a.data_ptr()), a
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        return a.ctypes.data_as(ctypes.c_void_p), a
+
+    def make_request(self, fk, measure, query: Query):
+        import numpy as np
+        pf, kf = self._host(fk)
+        pm, km = self._host(measure)
+        out = np.zeros(query.nout, dtype=np.int64)
+        n = fk.numel() if hasattr(fk, "numel") else np.asarray(fk).size
+        req = Request(pf, pm, n, query, out.ctypes.data_as(ctypes.c_void_p))
+        return req, (kf, km, out)
+
+    def submit(self, fk, measure, query: Query) -> int:
+        req, keep = self.make_request(fk, measure, query)
+        t = ctypes.c_uint64()
+        _check(lib().skx_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "skx_server_submit")
+        self._keep[t.value] = keep
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        st = lib().skx_server_wait(self._h, ticket, timeout_ms)
+        _check(st, "skx_server_wait")
+        out = self._keep.pop(ticket)[2]
+        lib().skx_server_release(self._h, ticket)
+        return out
+
+    def replay(self, requests, arrival_s, timeout_ms: int = 120000):
+        """requests: list of (Request, keep) from make_request; returns latencies in seconds."""
+        import numpy as np
+        arr = (Request * len(requests))(*[r for r, _ in requests])
+        t = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.zeros(len(requests), dtype=np.float64)
+        _check(lib().skx_server_replay(self._h, arr, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(requests),
+                                       timeout_ms, lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "skx_server_replay")
+        return lat
+
+    def stats(self):
+        r, n, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().skx_server_stats(self._h, ctypes.byref(r), ctypes.byref(n), ctypes.byref(m)), "skx_server_stats")
+        return {"rounds": r.value, "rows": n.value, "max_active": m.value}
+
+    def close(self):
+        if self._h:
+            lib().skx_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def skx_join_aggregate_host(rows, fk, measure, query: Query, out=None, stream=None):

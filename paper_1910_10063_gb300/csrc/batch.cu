@@ -25,16 +25,6 @@ namespace {
 
 using namespace pcore;
 
-struct BatchDesc {
-    const int32_t *fk;
-    const int32_t *measure;
-    unsigned long long *out;
-    int64_t F;
-    int32_t agg, fcol, flt, gcol, G, pcol;
-    int32_t vec;  // fk and measure 16-byte aligned: 16-byte loads
-    int32_t nout;
-};
-
 struct BatchArgs {
     const BatchDesc *desc;
     const uint32_t *tile_start;  // n + 1 entries
@@ -49,8 +39,9 @@ struct BatchArgs {
     unsigned *err;
 };
 
-__global__ void k_batch_clear(const BatchDesc *__restrict__ desc, int32_t n, uint32_t *counter) {
+__global__ void k_batch_clear(const BatchDesc *__restrict__ desc, int32_t n, uint32_t *counter, int clear_outputs) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+    if (!clear_outputs) return;
     for (int q = blockIdx.x; q < n; q += gridDim.x) {
         const BatchDesc d = desc[q];
         for (int g = threadIdx.x; g < d.nout; g += blockDim.x) d.out[g] = 0;
@@ -222,6 +213,69 @@ __global__ void __launch_bounds__(512) k_probe_batch(BatchArgs a) {
 constexpr int kBatchMaxGroups = 4096;
 
 }  // namespace
+
+int batch_row_path(const void *rows, int32_t row_bytes, bool cols_beyond16, bool cols_beyond8) {
+    if (row_bytes % 16 == 0 && aligned16(rows) && !cols_beyond16) return kRow16;
+    if (row_bytes == 8 && (reinterpret_cast<uintptr_t>(rows) & 7u) == 0 && !cols_beyond8) return kRow8;
+    return kRowGeneric;
+}
+
+cudaError_t launch_batch_items(const BatchDesc *d_desc, const uint32_t *d_tile_start, int32_t n,
+                               uint32_t total_tiles, int32_t tile_rows, const void *rows, int32_t N,
+                               int32_t row_bytes, int path, int32_t max_groups, const skx_tuning &t,
+                               bool clear_outputs, uint32_t *d_counter, cudaStream_t st) {
+    unsigned *err = device_error_word();
+    if (!err) return cudaErrorMemoryAllocation;
+    const int32_t t_hot = t.hot_keys > 0 ? t.hot_keys : 0;
+    const int32_t t_lane = t.lane_keys > 0 ? t.lane_keys : 0;
+    BatchArgs a{};
+    a.desc = d_desc;
+    a.tile_start = d_tile_start;
+    a.counter = d_counter;
+    a.n = n;
+    a.total_tiles = total_tiles;
+    a.tile_rows = tile_rows;
+    a.rows = static_cast<const char *>(rows);
+    a.N = N;
+    a.row_bytes = row_bytes;
+    a.max_groups = max_groups;
+    a.t_hot = t_hot;
+    a.t_lane = t_lane;
+    a.gather_policy = t.gather_policy;
+    a.err = err;
+    const size_t smem = size_t(max_groups + t_hot + t_lane * 32) * 8;
+    const int optin = device_max_smem_optin();
+    if (smem + 1024 > (size_t)optin) return cudaErrorInvalidValue;
+    const int block = t.block_threads;
+    int per_sm = 0;
+    auto go = [&](auto kern) -> cudaError_t {
+        static int configured = -1;
+        if (configured != optin) {
+            cudaFuncAttributes fa{};
+            cudaError_t e2 = cudaFuncGetAttributes(&fa, kern);
+            if (e2 != cudaSuccess) return e2;
+            // dynamic + static shared memory must fit the per-block limit
+            e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      optin - (int)fa.sharedSizeBytes);
+            if (e2 != cudaSuccess) return e2;
+            configured = optin;
+        }
+        cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+        if (e2 != cudaSuccess) return e2;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        if (t.ctas_per_sm > 0 && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;
+        int64_t grid = int64_t(device_sm_count()) * per_sm;
+        if (grid > int64_t(total_tiles)) grid = std::max<int64_t>(1, total_tiles);
+        k_batch_clear<<<std::max(1, std::min(n, 1024)), 256, 0, st>>>(d_desc, n, d_counter, clear_outputs ? 1 : 0);
+        kern<<<(unsigned)grid, block, smem, st>>>(a);
+        note_launches(2);
+        return cudaGetLastError();
+    };
+    if (path == kRow16) return go(k_probe_batch<kRow16>);
+    if (path == kRow8) return go(k_probe_batch<kRow8>);
+    return go(k_probe_batch<kRowGeneric>);
+}
+
 }  // namespace skx
 
 using namespace skx;
@@ -263,59 +317,8 @@ skx_status plan_tiles(skx_batch_plan *p, int32_t tile_rows, cudaStream_t st) {
 }
 
 skx_status plan_launch(skx_batch_plan *p, cudaStream_t st) {
-    unsigned *err = device_error_word();
-    if (!err) return SKX_ENOMEM;
-    skx_tuning t = p->t;
-    const int32_t t_hot = t.hot_keys > 0 ? t.hot_keys : 0;
-    const int32_t t_lane = t.lane_keys > 0 ? t.lane_keys : 0;
-    BatchArgs a{};
-    a.desc = p->d_desc;
-    a.tile_start = p->d_tile_start;
-    a.counter = p->d_counter;
-    a.n = p->n;
-    a.total_tiles = p->total_tiles;
-    a.tile_rows = p->tile_rows;
-    a.rows = static_cast<const char *>(p->rows);
-    a.N = p->N;
-    a.row_bytes = p->row_bytes;
-    a.max_groups = p->max_groups;
-    a.t_hot = t_hot;
-    a.t_lane = t_lane;
-    a.gather_policy = t.gather_policy;
-    a.err = err;
-    const size_t smem = size_t(p->max_groups + t_hot + t_lane * 32) * 8;
-    const int optin = device_max_smem_optin();
-    if (smem + 1024 > (size_t)optin) return SKX_EINVAL;
-    const int block = t.block_threads;
-    int per_sm = 0;
-    cudaError_t e;
-    auto go = [&](auto kern) -> cudaError_t {
-        static int configured = -1;
-        if (configured != optin) {
-            cudaFuncAttributes fa{};
-            cudaError_t e2 = cudaFuncGetAttributes(&fa, kern);
-            if (e2 != cudaSuccess) return e2;
-            // dynamic + static shared memory must fit the per-block limit
-            e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      optin - (int)fa.sharedSizeBytes);
-            if (e2 != cudaSuccess) return e2;
-            configured = optin;
-        }
-        cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
-        if (e2 != cudaSuccess) return e2;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        if (t.ctas_per_sm > 0 && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;
-        int64_t grid = int64_t(device_sm_count()) * per_sm;
-        if (grid > int64_t(p->total_tiles)) grid = std::max<int64_t>(1, p->total_tiles);
-        k_batch_clear<<<std::min(p->n, 1024), 256, 0, st>>>(p->d_desc, p->n, p->d_counter);
-        kern<<<(unsigned)grid, block, smem, st>>>(a);
-        note_launches(2);
-        return cudaGetLastError();
-    };
-    if (p->path == kRow16) e = go(k_probe_batch<kRow16>);
-    else if (p->path == kRow8) e = go(k_probe_batch<kRow8>);
-    else e = go(k_probe_batch<kRowGeneric>);
-    SKX_CUDA_TRY(e);
+    SKX_CUDA_TRY(launch_batch_items(p->d_desc, p->d_tile_start, p->n, p->total_tiles, p->tile_rows, p->rows, p->N,
+                                    p->row_bytes, p->path, p->max_groups, p->t, true, p->d_counter, st));
     return SKX_OK;
 }
 
@@ -383,9 +386,7 @@ skx_status skx_batch_plan_create(const void *d_rows, int32_t N, int32_t row_byte
     p->n = n;
     p->max_groups = max_groups;
     p->descs.assign(h_descs, h_descs + n);
-    p->path = kRowGeneric;
-    if (row_bytes % 16 == 0 && aligned16(d_rows) && !any_col_beyond16) p->path = kRow16;
-    else if (row_bytes == 8 && (reinterpret_cast<uintptr_t>(d_rows) & 7u) == 0 && !any_col_beyond8) p->path = kRow8;
+    p->path = batch_row_path(d_rows, row_bytes, any_col_beyond16, any_col_beyond8);
     skx_tuning t{};
     if (tuning) t = *tuning;
     ProbeArgs pa{};

@@ -167,6 +167,27 @@ struct ProbeArgs {
 void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t);
 cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t st);
 skx_status validate_query(const skx_query *q, int32_t row_bytes);
+// One unit of a batched probe launch (batch.cu): a query over a contiguous
+// range of remapped fact rows, accumulating into `out`.
+struct BatchDesc {
+    const int32_t *fk;
+    const int32_t *measure;
+    unsigned long long *out;
+    int64_t F;
+    int32_t agg, fcol, flt, gcol, G, pcol;
+    int32_t vec;  // fk and measure 16-byte aligned: 16-byte loads
+    int32_t nout;
+};
+
+// Row access path for a table (0 generic, 1 16-byte, 2 8-byte rows).
+int batch_row_path(const void *rows, int32_t row_bytes, bool cols_beyond16, bool cols_beyond8);
+// Enqueues the batched probe over n device descriptors and their tile table.
+// clear_outputs: zero every output first (else outputs accumulate).
+cudaError_t launch_batch_items(const BatchDesc *d_desc, const uint32_t *d_tile_start, int32_t n,
+                               uint32_t total_tiles, int32_t tile_rows, const void *rows, int32_t N,
+                               int32_t row_bytes, int path, int32_t max_groups, const skx_tuning &t,
+                               bool clear_outputs, uint32_t *d_counter, cudaStream_t st);
+
 // Autotuner cache lookup (autotune.cu).
 bool cached_probe_tuning(int32_t N, int32_t row_bytes, const skx_query &q, int64_t F, int remapped, skx_tuning *out);
 
