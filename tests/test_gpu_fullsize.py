@@ -1,0 +1,174 @@
+"""Parity at the full configured sizes, with the launch configurations bench.py
+times (autotuned probe, whole-row reorder, batched plan, serving loop).
+
+* 20M x 64-byte rows, 500M-row FK column: counts, perm, rank, remap and
+  reorder compared with the oracle element by element, and the probe result at
+  Zipf s in {0, 0.5, 1.0, 1.5} on the remapped layout compared with the oracle
+  on the original layout.
+* 200M x 64-byte rows, 1B-row FK column (the largest cache-fit size): properties
+  that hold at any size -- perm is a bijection with rank its inverse, counts
+  sum to F and are non-increasing along perm with ascending ids among equal
+  counts, sampled counts equal direct counts, COUNT equals the sum of the counts
+  of passing ids, and the plain and remapped probes agree.
+* 512 batched queries and 256 served requests against the resident index,
+  each compared with the oracle.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1910_10063_gb300 import synth  # noqa: E402
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1910_10063_gb300 as skx  # noqa: E402
+
+DEV = torch.device("cuda:0")
+N1, F1 = 20_000_000, 500_000_000
+THREADS = 16
+
+
+@pytest.fixture(scope="module")
+def large():
+    w = synth.DeviceWorkload(N1, F1, 1.0, seed=0, width=16, device=DEV)
+    yield w
+    del w
+    torch.cuda.empty_cache()
+
+
+def test_large_build_remap_reorder_exact(large):
+    w = large
+    idx = skx.skx_build_index(w.fk, N1)
+    fk2 = torch.empty_like(w.fk)
+    skx.skx_remap(idx, w.fk, fk2)
+    dim2 = torch.empty_like(w.dim)
+    skx.skx_reorder(idx, w.dim, dim2)
+    assert skx.skx_stream_status() == skx.SKX_OK
+    fk = w.fk.cpu().numpy()
+    cnt, perm, rank = oracle.build_index(fk, N1)
+    assert np.array_equal(idx.counts.cpu().numpy().view(np.uint32).astype(np.uint64), cnt)
+    assert np.array_equal(idx.perm.cpu().numpy(), perm)
+    assert np.array_equal(idx.rank.cpu().numpy(), rank)
+    assert np.array_equal(fk2.cpu().numpy(), oracle.remap(rank, fk))
+    assert np.array_equal(dim2.cpu().numpy(), oracle.reorder(perm, w.dim.cpu().numpy()))
+    idx.close()
+
+
+@pytest.mark.parametrize("s", [0.0, 0.5, 1.0, 1.5])
+def test_large_probe_exact(large, s):
+    w = large
+    fk = w.fk if s == 1.0 else synth.DeviceWorkload(N1, F1, s, seed=0, width=16, device=DEV, r2id=w.r2id_host,
+                                                     with_measure=False, with_dim=False).fk
+    idx = skx.skx_build_index(fk, N1)
+    fk2 = torch.empty_like(fk)
+    skx.skx_remap(idx, fk, fk2)
+    dim2 = torch.empty_like(w.dim)
+    skx.skx_reorder(idx, w.dim, dim2)
+    q = skx.Query.groupby_sum()
+    t, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True)
+    got = skx.skx_probe_aggregate(dim2, fk2, w.measure, q, tuning=t).cpu().numpy()
+    want = oracle.probe(w.dim.cpu().numpy(), fk.cpu().numpy(), w.measure.cpu().numpy(), nthreads=THREADS)
+    assert np.array_equal(got, want)
+    # the query copy path gives the same result
+    q8 = skx.skx_reorder_query(idx, w.dim, q)
+    got8 = skx.skx_probe_aggregate(q8, fk2, w.measure, skx.skx_query_prefiltered(q)).cpu().numpy()
+    assert np.array_equal(got8, want)
+    idx.close()
+    assert skx.skx_stream_status() == skx.SKX_OK
+
+
+def test_cachefit_largest_properties():
+    n, f = 200_000_000, 1_000_000_000
+    w = synth.DeviceWorkload(n, f, 1.0, seed=2, width=16, device=DEV)
+    idx = skx.skx_build_index(w.fk, n)
+    perm, rank = idx.perm, idx.rank
+    cnt = idx.counts.view(torch.int32).to(torch.int64)
+    ar = torch.arange(n, device=DEV, dtype=torch.int32)
+    assert torch.equal(torch.sort(perm).values, ar)                         # bijection
+    assert torch.equal(rank[perm.long()], ar)                               # rank is the inverse
+    assert int(cnt.sum()) == f
+    c_by_rank = cnt[perm.long()]
+    assert bool((c_by_rank[1:] <= c_by_rank[:-1]).all())                    # decreasing frequency
+    ties = c_by_rank[1:] == c_by_rank[:-1]
+    assert bool((perm[1:][ties] > perm[:-1][ties]).all())                   # ascending ids among ties
+    for v in np.random.default_rng(0).integers(0, n, 6).tolist() + [int(perm[0]), int(perm[1000])]:
+        assert int((w.fk == v).sum()) == int(cnt[v])                        # sampled direct counts
+    fk2 = torch.empty_like(w.fk)
+    skx.skx_remap(idx, w.fk, fk2)
+    dim2 = torch.empty_like(w.dim)
+    skx.skx_reorder(idx, w.dim, dim2)
+    for q in (skx.Query.groupby_sum(), skx.Query.count(), skx.Query.sum()):
+        a = skx.skx_probe_aggregate(w.dim, w.fk, w.measure, q, tuning=skx.Tuning.plain())
+        b = skx.skx_probe_aggregate(dim2, fk2, w.measure, q)
+        assert torch.equal(a, b)                                            # layout invariance
+    passing = w.dim[:, 1] < 50
+    count = skx.skx_probe_aggregate(dim2, fk2, w.measure, skx.Query.count())
+    assert int(count[0]) == int(cnt[passing].sum())                         # COUNT = sum of counts
+    assert skx.skx_stream_status() == skx.SKX_OK
+    idx.close()
+    del w, fk2, dim2
+    torch.cuda.empty_cache()
+
+
+def test_batched_queries_exact(large):
+    import bench
+    w = large
+
+    class A:
+        n = N1
+    queries = bench.batch_workload(A, w, DEV, 512)
+    idx = skx.skx_build_index(w.fk, N1)
+    dim2 = torch.empty_like(w.dim)
+    skx.skx_reorder(idx, w.dim, dim2)
+    items = []
+    for fk, m, q, _ in queries:
+        fk2 = torch.empty_like(fk)
+        skx.skx_remap(idx, fk, fk2)
+        items.append((fk2, m, q, torch.empty(q.nout, dtype=torch.int64, device=DEV)))
+    plan = skx.BatchPlan(dim2, items)
+    plan.autotune()
+    plan.launch(use_graph=True)
+    torch.cuda.synchronize()
+    dim_h = w.dim.cpu().numpy()
+    for (fk, m, q, _), (_, _, _, out) in zip(queries, items):
+        want = oracle.probe(dim_h, fk.cpu().numpy(), m.cpu().numpy(), q.agg, q.filter_col, q.filter_lt, q.group_col,
+                            q.num_groups, q.payload_col, nthreads=THREADS)
+        assert np.array_equal(out.cpu().numpy(), want)
+    plan.close()
+    idx.close()
+
+
+def test_served_requests_exact():
+    n = 50_000_000
+    ws = synth.DeviceWorkload(n, 25 * n, 1.0, seed=7, width=16, device=DEV, with_measure=False)
+    idx = skx.skx_build_index(ws.fk, n)
+    dim2 = torch.empty_like(ws.dim)
+    skx.skx_reorder(idx, ws.dim, dim2)
+    dim_h = ws.dim.cpu().numpy()
+    r2id = ws.r2id_host
+    del ws
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(9)
+    sizes = synth.lognormal_sizes(256, 11)
+    qdefs = [skx.Query.count(), skx.Query.sum(), skx.Query.groupby_sum()]
+    cdf = {s: torch.from_numpy(synth.zipf_cdf(n, s)).to(DEV) for s in (0.8, 1.0, 1.2)}
+    d_r2id = torch.from_numpy(r2id).to(DEV)
+    reqs = []
+    for i in range(256):
+        s = float(rng.choice([0.8, 1.0, 1.2]))
+        fk = synth.zipf_fk_device(cdf[s], d_r2id, 5000 + i, int(sizes[i])).cpu().pin_memory()
+        m = synth.measure_device(5000 + i, int(sizes[i]), device=DEV).cpu().pin_memory()
+        reqs.append((fk, m, qdefs[i % 3]))
+    srv = skx.Server(dim2, idx.rank, skx.ServerConfig(max_inflight=64))
+    tickets = [srv.submit(*r) for r in reqs]
+    for t, (fk, m, q) in zip(tickets, reqs):
+        want = oracle.probe(dim_h, fk.numpy(), m.numpy(), q.agg, q.filter_col, q.filter_lt, q.group_col,
+                            q.num_groups, q.payload_col, nthreads=THREADS)
+        assert np.array_equal(srv.wait(t), want)
+    srv.close()
+    idx.close()
