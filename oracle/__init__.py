@@ -18,6 +18,12 @@ Improved Query Performance" (ICDE 2020, arXiv 1910.10063):
 * ``probe``              FK gather + filter + aggregation (Sections I, IV-A;
                          threads over fact chunks with independent buffers,
                          Section IV-C)
+* ``topk_counts``        Q3a heavy hitters: counts of transformed ids < k
+                         (Sections I, IV-B)
+* ``select``             Q2: offsets of qualifying fact rows (Sections I, IV-A)
+* ``index_append``       maintenance: new rows appended as least frequent
+                         (Section III-A)
+* ``cache_hit_rate``     the stack-distance cache model (Section III-C)
 
 Every function has at least one pin in ``tests/test_oracle_pins.py`` that
 does not go through this code (worked example of Fig. 2, brute force, closed
@@ -56,7 +62,7 @@ def build(src: str = _SRC, out: str = _LIB, force: bool = False) -> str:
         return out
     tmp = out + f".tmp{os.getpid()}"
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
-                    "-o", tmp, src], check=True)
+                    "-o", tmp, src, "-lm"], check=True)
     os.replace(tmp, out)
     return out
 
@@ -83,8 +89,13 @@ def _declare(lib):
     lib.orc_remap.argtypes = [P, i32, P, i64, P]
     lib.orc_reorder.argtypes = [P, i32, P, i32, P]
     lib.orc_probe.argtypes = [P, i32, i32, P, P, i64, cint, cint, i32, cint, i32, cint, P, cint]
+    lib.orc_topk_counts.argtypes = [P, i64, i32, P]
+    lib.orc_select.argtypes = [P, i32, i32, P, i64, cint, i32, P, P]
+    lib.orc_index_append.argtypes = [P, P, i32, i32, P, P]
+    lib.orc_cache_hit_rate.argtypes = [P, i64, i64, P, P]
     for f in ("orc_histogram", "orc_sort_by_frequency", "orc_invert", "orc_build_index",
-              "orc_remap", "orc_reorder", "orc_probe"):
+              "orc_remap", "orc_reorder", "orc_probe", "orc_topk_counts", "orc_select", "orc_index_append",
+              "orc_cache_hit_rate"):
         getattr(lib, f).restype = cint
     return lib
 
@@ -184,3 +195,52 @@ def probe(rows, fk, measure, agg: int = AGG_GROUPBY_SUM, filter_col: int = 1,
     if st:
         raise OracleError(st, "probe")
     return out.view(np.int64)
+
+
+def topk_counts(fk_remapped, k: int, lib=None) -> np.ndarray:
+    lib = lib or load()
+    fk = _c(fk_remapped, np.int32)
+    out = np.zeros(k, dtype=np.uint64)
+    st = lib.orc_topk_counts(_ptr(fk), fk.shape[0], k, _ptr(out))
+    if st:
+        raise OracleError(st, "topk_counts")
+    return out
+
+
+def select(rows, fk, filter_col: int = 1, filter_lt: int = 50, lib=None) -> np.ndarray:
+    """uint32 offsets (increasing) of the fact rows whose dimension row passes col < c."""
+    lib = lib or load()
+    rows = _c(rows, np.int32)
+    fk = _c(fk, np.int32)
+    offs = np.zeros(max(fk.shape[0], 1), dtype=np.uint32)
+    cnt = np.zeros(1, dtype=np.int64)
+    st = lib.orc_select(_ptr(rows), rows.shape[0], rows.shape[1], _ptr(fk), fk.shape[0], filter_col, filter_lt,
+                        _ptr(offs), _ptr(cnt))
+    if st:
+        raise OracleError(st, "select")
+    return offs[:int(cnt[0])].copy()
+
+
+def index_append(perm, rank, n_new: int, lib=None):
+    lib = lib or load()
+    perm = _c(perm, np.int32)
+    rank = _c(rank, np.int32)
+    n = perm.shape[0]
+    po = np.zeros(n + n_new, dtype=np.int32)
+    ro = np.zeros(n + n_new, dtype=np.int32)
+    st = lib.orc_index_append(_ptr(perm), _ptr(rank), n, n_new, _ptr(po), _ptr(ro))
+    if st:
+        raise OracleError(st, "index_append")
+    return po, ro
+
+
+def cache_hit_rate(f, S: int, lib=None):
+    """(hit rate, cdf per line) of the Section III-C model for line frequencies f and S lines."""
+    lib = lib or load()
+    f = _c(f, np.float64)
+    hit = np.zeros(1, dtype=np.float64)
+    cdf = np.zeros(f.shape[0], dtype=np.float64)
+    st = lib.orc_cache_hit_rate(_ptr(f), f.shape[0], S, _ptr(hit), _ptr(cdf))
+    if st:
+        raise OracleError(st, "cache_hit_rate")
+    return float(hit[0]), cdf

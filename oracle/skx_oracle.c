@@ -39,6 +39,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <pthread.h>
+#include <math.h>
 
 #define ORC_OK 0
 #define ORC_EINVAL 1
@@ -293,4 +294,139 @@ int orc_probe(const int32_t *rows, int32_t N, int32_t row_words,
     }
     free(jobs); free(bufs); free(tids);
     return status;
+}
+
+/* ------------------------------------------------------------------------
+ * Heavy-hitter counts (Section I, query Q3a; Section IV-B): with an up-to-date
+ * index the k most frequent values are the transformed ids 0..k-1, so the
+ * query counts only those: out[r] = #{i : fk_remapped[i] == r}, r < k.  Keys
+ * outside [0, k) are ignored.
+ */
+int orc_topk_counts(const int32_t *fk_remapped, int64_t F, int32_t k, uint64_t *out)
+{
+    if (F < 0 || k < 1 || !out || (F > 0 && !fk_remapped))
+        return ORC_EINVAL;
+    for (int32_t r = 0; r < k; r++)
+        out[r] = 0;
+    for (int64_t i = 0; i < F; i++) {
+        int32_t r = fk_remapped[i];
+        if (r >= 0 && r < k)
+            out[r] += 1;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Selection (Section I, query Q2; Section IV-A): the offsets i, in increasing
+ * order, of the fact rows whose dimension row passes "col < c"; *count is
+ * their number.  offsets must hold F entries.
+ */
+int orc_select(const int32_t *rows, int32_t N, int32_t row_words, const int32_t *fk, int64_t F,
+               int filter_col, int32_t filter_lt, uint32_t *offsets, int64_t *count)
+{
+    if (F < 0 || N < 0 || row_words <= 0 || filter_col < 0 || filter_col >= row_words || !count ||
+        (F > 0 && (!rows || !fk || !offsets)))
+        return ORC_EINVAL;
+    int64_t c = 0;
+    for (int64_t i = 0; i < F; i++) {
+        int32_t v = fk[i];
+        if (v < 0 || v >= N)
+            return ORC_EKEY;
+        if (rows[(size_t)v * (size_t)row_words + (size_t)filter_col] < filter_lt)
+            offsets[c++] = (uint32_t)i;
+    }
+    *count = c;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Index maintenance (Section III-A): n_new dimension rows appended to a
+ * table of N rows get the ids N..N+n_new-1 and enter the permutation index at
+ * its end as the new least frequent items; existing ranks are unchanged.
+ */
+int orc_index_append(const int32_t *perm, const int32_t *rank, int32_t N, int32_t n_new,
+                     int32_t *perm_out, int32_t *rank_out)
+{
+    if (N < 0 || n_new < 0 || (N > 0 && (!perm || !rank)) || !perm_out || !rank_out)
+        return ORC_EINVAL;
+    for (int32_t r = 0; r < N; r++) {
+        perm_out[r] = perm[r];
+        rank_out[r] = rank[r];
+    }
+    for (int32_t j = 0; j < n_new; j++) {
+        perm_out[N + j] = N + j;
+        rank_out[N + j] = N + j;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Cache model (Section III-C).  f[0..L) are the access frequencies of L cache
+ * lines (sum 1), S the cache size in lines.  For line i and k trials, each
+ * other line j is expected n_j = k f_j / (1 - f_i) times; the number of
+ * distinct lines is d(k) = k - sum_{j != i} max(0, n_j - 1).  K_i is found by
+ * binary search over k >= S as the smallest k with d(k) >= S (K_i is infinite
+ * when d never reaches S, i.e. when fewer than S other lines are ever used);
+ * cdf_i = 1 - (1 - f_i)^K_i and the hit rate is sum_i f_i cdf_i.  Plain
+ * O(L) evaluation of d(k).  cdf may be NULL.
+ */
+static double orc_cache_d(const double *f, int64_t L, int64_t i, double k)
+{
+    double fi = f[i], rep = 0.0;
+    for (int64_t j = 0; j < L; j++) {
+        if (j == i)
+            continue;
+        double n = k * f[j] / (1.0 - fi);
+        if (n > 1.0)
+            rep += n - 1.0;
+    }
+    return k - rep;
+}
+
+int orc_cache_hit_rate(const double *f, int64_t L, int64_t S, double *hit, double *cdf)
+{
+    if (!f || L < 1 || S < 1 || !hit)
+        return ORC_EINVAL;
+    int64_t used = 0;
+    double fmin = 1.0;
+    for (int64_t j = 0; j < L; j++) {
+        if (f[j] < 0.0)
+            return ORC_EINVAL;
+        if (f[j] > 0.0) {
+            used++;
+            if (f[j] < fmin)
+                fmin = f[j];
+        }
+    }
+    double h = 0.0;
+    for (int64_t i = 0; i < L; i++) {
+        double c;
+        int64_t others = used - (f[i] > 0.0 ? 1 : 0);
+        if (f[i] <= 0.0) {
+            c = 0.0;
+        } else if (f[i] >= 1.0) {
+            c = 1.0;
+        } else if (others < S) {
+            c = 1.0; /* d(k) <= others < S for every k: never evicted */
+        } else {
+            /* d(k) is non-decreasing and reaches `others` once every n_j >= 1 */
+            double lo = (double)S, hi = (double)S;
+            while (orc_cache_d(f, L, i, hi) < (double)S)
+                hi = hi * 2.0 + 1.0 / fmin;
+            while (hi - lo > 0.5) { /* integer binary search for the smallest k with d(k) >= S */
+                double mid = floor((lo + hi) / 2.0);
+                if (orc_cache_d(f, L, i, mid) >= (double)S)
+                    hi = mid;
+                else
+                    lo = mid + 1.0;
+            }
+            double K = lo;
+            c = 1.0 - pow(1.0 - f[i], K);
+        }
+        if (cdf)
+            cdf[i] = c;
+        h += f[i] * c;
+    }
+    *hit = h;
+    return ORC_OK;
 }

@@ -264,6 +264,90 @@ def pin_probe_errors(lib):
             raise AssertionError("error not reported")
 
 
+# ------------------------------------------------------------------ Q3a, Q2, maintenance, cache model
+def pin_topk_counts(lib):
+    rng = np.random.default_rng(10)
+    n, f, k = 3000, 50_000, 100
+    fk = (rng.zipf(1.2, f) % n).astype(np.int32)
+    cnt, perm, rank = oracle.build_index(fk, n, lib=lib)
+    fk2 = oracle.remap(rank, fk, lib=lib)
+    top = oracle.topk_counts(fk2, k, lib=lib)
+    c = collections.Counter(fk2.tolist())
+    assert [int(x) for x in top] == [c.get(r, 0) for r in range(k)]   # brute force
+    assert np.array_equal(top, cnt[perm[:k]])                          # ranks < k are the k most frequent
+    assert np.all(np.diff(top.astype(np.int64)) <= 0)
+    assert oracle.topk_counts(np.array([-1, 5, 2, 2], dtype=np.int32), 3, lib=lib).tolist() == [0, 0, 2]
+
+
+def pin_select(lib):
+    rng = np.random.default_rng(11)
+    n, f = 40, 500
+    rows = np.stack([rng.integers(0, 5, n), rng.integers(0, 10, n)], axis=1).astype(np.int32)
+    fk = rng.integers(0, n, f).astype(np.int32)
+    for c in (0, 3, 5, 10):
+        got = oracle.select(rows, fk, 1, c, lib=lib)
+        want = [i for i in range(f) if rows[fk[i], 1] < c]
+        assert got.tolist() == want
+        count = oracle.probe(rows, fk, None, oracle.AGG_COUNT, 1, c, 0, 1, -1, lib=lib)
+        assert int(count[0]) == len(want)                              # Q2 count == COUNT query
+    eq = rows.copy(); eq[:, 1] = 3
+    assert oracle.select(eq, fk, 1, 3, lib=lib).size == 0              # strict "<"
+
+
+def pin_index_append(lib):
+    rng = np.random.default_rng(12)
+    perm = rng.permutation(50).astype(np.int32)
+    rank = np.argsort(perm).astype(np.int32)
+    p2, r2 = oracle.index_append(perm, rank, 7, lib=lib)
+    assert p2.tolist() == perm.tolist() + list(range(50, 57))
+    assert np.array_equal(r2[p2], np.arange(57))
+    assert np.array_equal(r2[:50], rank)
+
+
+def _lru_hit_rate(p, S, n_acc, seed):
+    rng = np.random.default_rng(seed)
+    acc = rng.choice(p.size, size=n_acc, p=p)
+    od, hits = collections.OrderedDict(), 0
+    for a in acc.tolist():
+        if a in od:
+            hits += 1
+            od.move_to_end(a)
+        else:
+            od[a] = None
+            if len(od) > S:
+                od.popitem(last=False)
+    return hits / n_acc
+
+
+def pin_cache_model(lib):
+    # S = 1: d(1) = 1 for every line, so K = 1 and the model is exact LRU: sum of f_i^2
+    f = np.array([0.5, 0.3, 0.15, 0.05])
+    hit, cdf = oracle.cache_hit_rate(f, 1, lib=lib)
+    assert abs(hit - float(np.sum(f * f))) < 1e-12 and np.allclose(cdf, f)
+    # uniform lines: n_j <= 1 up to k = L - 1, so K = S and hit = 1 - (1 - 1/L)^S
+    for L, S in ((100, 50), (1000, 10), (64, 63)):
+        hit, _ = oracle.cache_hit_rate(np.full(L, 1.0 / L), S, lib=lib)
+        assert abs(hit - (1 - (1 - 1.0 / L) ** S)) < 1e-12
+    # worked by hand: f = (0.9, 0.07, 0.015, 0.01, 0.005), S = 3.  Hot line: n_j = k f_j / 0.1 =
+    # k (0.7, 0.15, 0.1, 0.05), so d(6) = 6 - 3.2 = 2.8 < 3 <= d(7) = 7 - 3.9 - 0.05 = 3.05 -> K = 7.
+    _, cdf = oracle.cache_hit_rate(np.array([0.9, 0.07, 0.015, 0.01, 0.005]), 3, lib=lib)
+    assert abs(cdf[0] - (1 - 0.1 ** 7)) < 1e-12
+    # a cache holding every used line never misses
+    assert oracle.cache_hit_rate(np.array([0.6, 0.4, 0.0]), 2, lib=lib)[0] == 1.0
+    assert oracle.cache_hit_rate(np.array([1.0]), 1, lib=lib)[0] == 1.0
+    # more cache never hurts
+    z = 1.0 / np.arange(1, 301)
+    z /= z.sum()
+    hits = [oracle.cache_hit_rate(z, S, lib=lib)[0] for S in (1, 5, 20, 80, 200)]
+    assert all(b >= a for a, b in zip(hits, hits[1:]))
+    # within the paper's stated error (< 5 %) of a simulated LRU cache on Zipf traces
+    for s, L, S in ((1.0, 2000, 200), (0.5, 2000, 100), (1.5, 2000, 50)):
+        p = 1.0 / np.arange(1, L + 1) ** s
+        p /= p.sum()
+        assert abs(oracle.cache_hit_rate(p, S, lib=lib)[0] - _lru_hit_rate(p, S, 200_000, 1)) < 0.05
+
+
 ALL_PINS = [pin_fig2_example, pin_histogram, pin_sort_by_frequency, pin_invert, pin_remap,
             pin_reorder, pin_probe_brute_force, pin_probe_closed_forms, pin_probe_wraparound,
-            pin_probe_layout_invariance, pin_probe_errors]
+            pin_probe_layout_invariance, pin_probe_errors, pin_topk_counts, pin_select, pin_index_append,
+            pin_cache_model]

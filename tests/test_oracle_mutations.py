@@ -25,6 +25,13 @@ MUTATIONS = [
     ("product_in_32_bits", "(uint64_t)((int64_t)j->measure[i] * p)", "(uint64_t)(int64_t)(int32_t)((int64_t)j->measure[i] * p)"),
     ("histogram_double_count", "cnt[v] += 1;", "cnt[v] += 1 + (v == 0);"),
     ("group_from_filter_column", "int32_t g = row[j->group_col];", "int32_t g = row[j->filter_col] % j->G;"),
+    ("topk_drops_rank_zero", "if (r >= 0 && r < k)", "if (r > 0 && r < k)"),
+    ("topk_off_by_one", "out[r] += 1;", "out[r > 0 ? r - 1 : 0] += 1;"),
+    ("select_not_strict", "+ (size_t)filter_col] < filter_lt)", "+ (size_t)filter_col] <= filter_lt)"),
+    ("select_wrong_offset", "offsets[c++] = (uint32_t)i;", "offsets[c++] = (uint32_t)v;"),
+    ("append_new_ids_first", "perm_out[N + j] = N + j;", "perm_out[N + j] = j;"),
+    ("cache_model_no_normalisation", "double n = k * f[j] / (1.0 - fi);", "double n = k * f[j];"),
+    ("cache_model_cdf_exponent", "c = 1.0 - pow(1.0 - f[i], K);", "c = 1.0 - pow(1.0 - f[i], K + 1.0);"),
     ("thread_merge_drops_last", "for (int t = 0; t < nthreads; t++) {\n        if (jobs[t].status",
      "for (int t = 0; t < nthreads - (nthreads > 1); t++) {\n        if (jobs[t].status"),
 ]
