@@ -143,6 +143,17 @@ skx_status skx_index_rank(const skx_index *idx, const int32_t **d_rank);     /* 
 skx_status skx_index_counts(const skx_index *idx, const uint32_t **d_counts); /* uint32[N] */
 int32_t skx_index_size(const skx_index *idx);                                /* N, or -1 */
 
+/*
+ * Index maintenance (Section III-A): n_new dimension rows appended to the
+ * table get the ids N .. N+n_new-1 and join the index at its end as the new
+ * least frequent items (count 0); existing ranks do not change, so remapped
+ * fact columns stay valid.  Reallocates the index arrays in stream order on
+ * `stream` (borrowed pointers from skx_index_perm/rank/counts become invalid).
+ * Fact inserts and deletes are not tracked: results stay exact with a stale
+ * index, only the layout's benefit fades until skx_build_index is run again.
+ */
+skx_status skx_index_append(skx_index *idx, int32_t n_new, void *stream);
+
 /* Frees the index (stream-ordered on the stream it was built on). NULL is a no-op. */
 void skx_index_destroy(skx_index *idx);
 
@@ -261,6 +272,34 @@ skx_status skx_probe_default_tuning(int32_t N, int32_t row_bytes, int64_t F, con
 skx_status skx_probe_autotune(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
                               const int32_t *d_measure, int64_t F, const skx_query *q, int remapped,
                               int64_t *d_out, void *stream, skx_tuning *out, float *best_ms);
+
+/* ------------------------------------------------------------------------
+ * The paper's other operators over the remapped layout.
+ * ------------------------------------------------------------------------ */
+
+/* Heavy hitters (query Q3a, Sections I and IV-B): with an up-to-date index the
+ * k most frequent values are the transformed ids 0..k-1, so d_out[r] (int64,
+ * k entries, fully overwritten) = #{i : d_fk[i] == r} for r < k and keys
+ * >= k are skipped.  The ids are perm[0..k).  Counters stay in shared memory
+ * for k up to about 55K. */
+skx_status skx_topk_counts(const int32_t *d_fk, int64_t F, int32_t k, int64_t *d_out, void *stream);
+
+/* Selection bitmap (query Q2 preprocessing, Section I): bit r of d_bits
+ * (uint32 words, ceil(N/32) of them) = row r's column filter_col < filter_lt. */
+skx_status skx_select_bitmap(const void *d_rows, int32_t N, int32_t row_bytes, int32_t filter_col, int32_t filter_lt,
+                             uint32_t *d_bits, void *stream);
+
+/* Selection (query Q2, Sections I and IV-A): writes the offsets i of the fact
+ * rows with bit d_fk[i] set, in increasing order, to d_offsets (uint32, room
+ * for F) and their number to *d_count (device int64).  Keys outside [0, N)
+ * are not selected and raise SKX_EKEYRANGE at skx_stream_status.  Uses
+ * stream-ordered scratch of about F/2048 bytes. */
+skx_status skx_select(const uint32_t *d_bits, int32_t N, const int32_t *d_fk, int64_t F, uint32_t *d_offsets,
+                      int64_t *d_count, void *stream);
+
+/* Cache model (Section III-C), host only: estimated LRU hit rate of a cache of
+ * S lines for L lines with access frequencies h_f (host, sum 1). */
+skx_status skx_cache_hit_rate(const double *h_f, int64_t L, int64_t S, double *hit);
 
 /* ------------------------------------------------------------------------
  * Batched probes (many queries, one persistent launch).  Each descriptor is

@@ -365,21 +365,29 @@ int orc_index_append(const int32_t *perm, const int32_t *rank, int32_t N, int32_
  * lines (sum 1), S the cache size in lines.  For line i and k trials, each
  * other line j is expected n_j = k f_j / (1 - f_i) times; the number of
  * distinct lines is d(k) = k - sum_{j != i} max(0, n_j - 1).  K_i is found by
- * binary search over k >= S as the smallest k with d(k) >= S (K_i is infinite
- * when d never reaches S, i.e. when fewer than S other lines are ever used);
+ * binary search over k >= S as the smallest k with d(k) >= S, equality taken up
+ * to rounding (relative 1e-9); K_i is infinite when d never reaches S, i.e.
+ * when fewer than S other lines are ever used;
  * cdf_i = 1 - (1 - f_i)^K_i and the hit rate is sum_i f_i cdf_i.  Plain
  * O(L) evaluation of d(k).  cdf may be NULL.
  */
-static double orc_cache_d(const double *f, int64_t L, int64_t i, double k)
+static double orc_cache_d(const double *f, int64_t L, int64_t i, double k, int64_t others)
 {
     double fi = f[i], rep = 0.0;
+    int64_t repeating = 0;
     for (int64_t j = 0; j < L; j++) {
         if (j == i)
             continue;
         double n = k * f[j] / (1.0 - fi);
-        if (n > 1.0)
+        if (n > 1.0) {
             rep += n - 1.0;
+            repeating++;
+        }
     }
+    /* once every other used line repeats, sum_{j != i} n_j = k exactly and
+     * d(k) = others; computing it directly avoids cancellation at large k */
+    if (repeating == others)
+        return (double)others;
     return k - rep;
 }
 
@@ -388,14 +396,14 @@ int orc_cache_hit_rate(const double *f, int64_t L, int64_t S, double *hit, doubl
     if (!f || L < 1 || S < 1 || !hit)
         return ORC_EINVAL;
     int64_t used = 0;
-    double fmin = 1.0;
+    double f_pos_min = 1.0;
     for (int64_t j = 0; j < L; j++) {
         if (f[j] < 0.0)
             return ORC_EINVAL;
         if (f[j] > 0.0) {
             used++;
-            if (f[j] < fmin)
-                fmin = f[j];
+            if (f[j] < f_pos_min)
+                f_pos_min = f[j];
         }
     }
     double h = 0.0;
@@ -409,19 +417,31 @@ int orc_cache_hit_rate(const double *f, int64_t L, int64_t S, double *hit, doubl
         } else if (others < S) {
             c = 1.0; /* d(k) <= others < S for every k: never evicted */
         } else {
-            /* d(k) is non-decreasing and reaches `others` once every n_j >= 1 */
+            /* d(k) is non-decreasing and reaches `others` once every n_j >= 1.
+             * "d(K) = S" is read as equality up to rounding: d >= S (1 - 1e-9).
+             * K is capped at 64 / f_i, where 1 - (1 - f_i)^K differs from 1 by
+             * less than e^-64. */
+            const double target = (double)S * (1.0 - 1e-9);
+            const double kmax = ceil(64.0 / f[i]) + (double)S;
             double lo = (double)S, hi = (double)S;
-            while (orc_cache_d(f, L, i, hi) < (double)S)
-                hi = hi * 2.0 + 1.0 / fmin;
-            while (hi - lo > 0.5) { /* integer binary search for the smallest k with d(k) >= S */
-                double mid = floor((lo + hi) / 2.0);
-                if (orc_cache_d(f, L, i, mid) >= (double)S)
-                    hi = mid;
-                else
-                    lo = mid + 1.0;
+            while (hi < kmax && orc_cache_d(f, L, i, hi, others) < target) {
+                hi = hi * 2.0 + 1.0 / f_pos_min;
+                if (hi > kmax)
+                    hi = kmax;
             }
-            double K = lo;
-            c = 1.0 - pow(1.0 - f[i], K);
+            if (orc_cache_d(f, L, i, hi, others) < target) {
+                c = 1.0; /* d never reaches S before the cap */
+            } else {
+                while (hi - lo >= 1.0) { /* integer binary search for the smallest k with d(k) >= S */
+                    double mid = lo + floor((hi - lo) / 2.0);
+                    if (orc_cache_d(f, L, i, mid, others) >= target)
+                        hi = mid;
+                    else
+                        lo = mid + 1.0;
+                }
+                double K = lo;
+                c = 1.0 - pow(1.0 - f[i], K);
+            }
         }
         if (cdf)
             cdf[i] = c;

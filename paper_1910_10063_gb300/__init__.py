@@ -170,6 +170,12 @@ def lib():
                                            ctypes.POINTER(ctypes.c_uint64)]
             L.skx_server_stats.restype = st
             L.skx_server_destroy.argtypes = [P]; L.skx_server_destroy.restype = None
+            L.skx_index_append.argtypes = [P, i32, P]; L.skx_index_append.restype = st
+            L.skx_topk_counts.argtypes = [P, i64, i32, P, P]; L.skx_topk_counts.restype = st
+            L.skx_select_bitmap.argtypes = [P, i32, i32, i32, i32, P, P]; L.skx_select_bitmap.restype = st
+            L.skx_select.argtypes = [P, i32, P, i64, P, P, P]; L.skx_select.restype = st
+            L.skx_cache_hit_rate.argtypes = [P, i64, i64, ctypes.POINTER(ctypes.c_double)]
+            L.skx_cache_hit_rate.restype = st
             L.skx_join_aggregate_host.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), P, P]
             L.skx_join_aggregate_host.restype = st
             _lib = L
@@ -528,6 +534,54 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def skx_index_append(index: Index, n_new: int, stream=None) -> Index:
+    _check(lib().skx_index_append(index._h, int(n_new), _stream(stream)), "skx_index_append")
+    index.n += int(n_new)
+    return index
+
+
+def skx_topk_counts(fk, k: int, out=None, stream=None):
+    """int64[k] counts of the transformed ids 0..k-1 (the k heavy hitters)."""
+    import torch
+    if out is None:
+        out = torch.empty(k, dtype=torch.int64, device=fk.device)
+    _check(lib().skx_topk_counts(_dptr(fk, "fk", torch.int32), fk.numel(), int(k), _dptr(out, "out", torch.int64),
+                                 _stream(stream)), "skx_topk_counts")
+    return out
+
+
+def skx_select_bitmap(rows, filter_col: int = 1, filter_lt: int = 50, out=None, stream=None):
+    import torch
+    n = rows.shape[0]
+    if out is None:
+        out = torch.empty((n + 31) // 32, dtype=torch.int32, device=rows.device)
+    _check(lib().skx_select_bitmap(_dptr(rows, "rows"), n, _row_bytes(rows), int(filter_col), int(filter_lt),
+                                   _dptr(out, "bits"), _stream(stream)), "skx_select_bitmap")
+    return out
+
+
+def skx_select(bits, n: int, fk, offsets=None, count=None, stream=None):
+    """(offsets int32 view of uint32[F], count int64[1]) of the qualifying fact rows, in order."""
+    import torch
+    if offsets is None:
+        offsets = torch.empty(max(fk.numel(), 1), dtype=torch.int32, device=fk.device)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int64, device=fk.device)
+    _check(lib().skx_select(_dptr(bits, "bits"), int(n), _dptr(fk, "fk", torch.int32), fk.numel(),
+                            _dptr(offsets, "offsets"), _dptr(count, "count", torch.int64), _stream(stream)),
+           "skx_select")
+    return offsets, count
+
+
+def skx_cache_hit_rate(f, S: int) -> float:
+    import numpy as np
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    hit = ctypes.c_double()
+    _check(lib().skx_cache_hit_rate(f.ctypes.data_as(ctypes.c_void_p), f.size, int(S), ctypes.byref(hit)),
+           "skx_cache_hit_rate")
+    return hit.value
 
 
 def skx_join_aggregate_host(rows, fk, measure, query: Query, out=None, stream=None):

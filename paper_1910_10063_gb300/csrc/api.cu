@@ -2,7 +2,9 @@
 // Argument checking, the index object, stream-ordered allocation and the
 // per-device data-error word; every step of the path runs in the kernels of
 // histogram.cu, sort.cu, remap.cu and probe.cu.
+#include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -94,6 +96,16 @@ int device_max_smem_optin() {
 }  // namespace skx
 
 using namespace skx;
+
+namespace skx_append {
+__global__ void k_append_tail(int32_t *perm, int32_t *rank, uint32_t *counts, int32_t N, int32_t n_new) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n_new; j += int64_t(gridDim.x) * blockDim.x) {
+        perm[N + j] = N + (int32_t)j;
+        rank[N + j] = N + (int32_t)j;
+        counts[N + j] = 0;
+    }
+}
+}  // namespace skx_append
 
 namespace {
 
@@ -233,6 +245,51 @@ void skx_index_destroy(skx_index *idx) {
     if (idx->rank) cudaFreeAsync(idx->rank, idx->stream);
     if (prev != idx->device) cudaSetDevice(prev);
     delete idx;
+}
+
+skx_status skx_index_append(skx_index *idx, int32_t n_new, void *stream) {
+    if (!idx || n_new < 0 || int64_t(idx->N) + n_new > INT32_MAX) return SKX_EINVAL;
+    if (n_new == 0) return SKX_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int32_t N = idx->N, N2 = N + n_new;
+    uint32_t *c2 = nullptr;
+    int32_t *p2 = nullptr, *r2 = nullptr;
+    const size_t nb = size_t(N2) * 4, ob = size_t(N) * 4;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&c2), nb, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&p2), nb, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&r2), nb, st);
+    // the index arrays were last written on the build stream: order against it first
+    cudaEvent_t ev = nullptr;
+    if (e == cudaSuccess && idx->stream != st) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, idx->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c2, idx->counts, ob, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p2, idx->perm, ob, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r2, idx->rank, ob, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+        const int64_t g = std::min<int64_t>((n_new + 255) / 256, int64_t(device_sm_count()) * 8);
+        skx_append::k_append_tail<<<(unsigned)std::max<int64_t>(g, 1), 256, 0, st>>>(p2, r2, c2, N, n_new);
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    if (ev) cudaEventDestroy(ev);
+    if (e != cudaSuccess) {
+        if (c2) cudaFreeAsync(c2, st);
+        if (p2) cudaFreeAsync(p2, st);
+        if (r2) cudaFreeAsync(r2, st);
+        return cuda_status(e);
+    }
+    cudaFreeAsync(idx->counts, st);
+    cudaFreeAsync(idx->perm, st);
+    cudaFreeAsync(idx->rank, st);
+    idx->counts = c2;
+    idx->perm = p2;
+    idx->rank = r2;
+    idx->N = N2;
+    idx->stream = st;
+    return SKX_OK;
 }
 
 skx_status skx_remap(const skx_index *idx, const int32_t *d_fk_in, int32_t *d_fk_out, int64_t F, void *stream) {

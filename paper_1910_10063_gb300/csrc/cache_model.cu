@@ -1,0 +1,105 @@
+// cache_model.cu -- the stack-distance cache model of Section III-C (host code).
+//
+// For L cache lines with access frequencies f_i and an LRU cache of S lines,
+// line i's next reference is modelled as geometric with p = f_i.  Within k
+// trials every other line j is expected n_j = k f_j / (1 - f_i) times, so the
+// number of distinct lines seen is d(k) = k - sum_{j != i} max(0, n_j - 1).
+// K_i is the smallest k >= S with d(k) >= S, equality taken up to rounding
+// (relative 1e-9), found by binary search (infinite when fewer than S other
+// lines are ever used), cdf_i = 1 - (1 - f_i)^K_i, and
+// the estimated hit rate is sum_i f_i cdf_i.
+//
+// Fast evaluation: with the frequencies sorted in decreasing order g and
+// prefix sums P, the lines with n_j > 1 are the prefix g_j > (1 - f_i) / k,
+// so d(k) costs one binary search.  Lines are visited hottest first; past the
+// hot lines that count among their own repeats, K_i can only fall as f_i
+// falls and never below its value at f = 0, so once it reaches that value
+// every colder line shares it.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "skx_internal.cuh"
+
+namespace {
+
+struct Model {
+    std::vector<double> g;  // frequencies, decreasing
+    std::vector<double> P;  // P[m] = g[0] + ... + g[m-1]
+    int64_t used = 0;       // lines with f > 0
+
+    // d(k) for a line of frequency fi that sits in g (self = true) or not.
+    double d(double k, double fi, bool self) const {
+        const double thr = (1.0 - fi) / k;  // n_j > 1  <=>  g_j > thr
+        const int64_t m = std::upper_bound(g.begin(), g.end(), thr, std::greater<double>()) - g.begin();
+        const bool self_in = self && fi > thr;
+        const int64_t others = used - (self ? 1 : 0);
+        // once every other used line repeats, sum_{j != i} n_j = k exactly and d = others
+        if (m - (self_in ? 1 : 0) >= others) return double(others);
+        double rep = (k / (1.0 - fi)) * P[m] - double(m);
+        if (self_in) rep -= k * fi / (1.0 - fi) - 1.0;  // line i is not one of "the others"
+        return k - rep;
+    }
+
+    // smallest integer k >= S with d(k) >= S (up to rounding), or infinity when it
+    // is not reached before 64 / f (where 1 - (1 - f)^k is 1 to within e^-64)
+    double K(double fi, bool self, int64_t S, double hi_hint, double fpos_min) const {
+        const int64_t others = used - (self ? 1 : 0);
+        if (others < S) return INFINITY;
+        const double target = double(S) * (1.0 - 1e-9);
+        const double kmax = std::ceil(64.0 / (fi > 0.0 ? fi : fpos_min)) + double(S);
+        double lo = double(S), hi = std::min(kmax, std::max(double(S), hi_hint));
+        while (hi < kmax && d(hi, fi, self) < target) hi = std::min(kmax, hi * 2.0 + 1.0);
+        if (d(hi, fi, self) < target) return INFINITY;
+        while (hi - lo >= 1.0) {
+            const double mid = lo + std::floor((hi - lo) / 2.0);
+            if (d(mid, fi, self) >= target) hi = mid;
+            else lo = mid + 1.0;
+        }
+        return lo;
+    }
+};
+
+}  // namespace
+
+extern "C" skx_status skx_cache_hit_rate(const double *h_f, int64_t L, int64_t S, double *hit) {
+    if (!h_f || L < 1 || S < 1 || !hit) return SKX_EINVAL;
+    Model m;
+    m.g.assign(h_f, h_f + L);
+    for (double x : m.g)
+        if (!(x >= 0.0)) return SKX_EINVAL;
+    std::sort(m.g.begin(), m.g.end(), std::greater<double>());
+    m.P.assign(L + 1, 0.0);
+    for (int64_t j = 0; j < L; ++j) m.P[j + 1] = m.P[j] + m.g[j];
+    m.used = std::lower_bound(m.g.begin(), m.g.end(), 0.0, std::greater<double>()) - m.g.begin();  // g > 0
+    // K at the limit f_i -> 0.  Every line i that is not among its own repeated
+    // lines (f_i K_i <= 1 - f_i) has d_i(k) <= d_floor(k), so K_i >= k_floor, and
+    // for such lines K_i does not increase as f_i decreases; colder lines then
+    // satisfy the same condition.  So once such a line has K_i == k_floor,
+    // every colder line has K = k_floor too.
+    const double fpos_min = m.used ? m.g[m.used - 1] : 1.0;  // smallest positive frequency
+    const double k_floor = m.K(0.0, false, S, double(S), fpos_min);
+    double h = 0.0, k_prev = INFINITY;
+    bool at_floor = false, monotone = false;
+    for (int64_t i = 0; i < m.used; ++i) {  // hottest first; zero-frequency lines add nothing
+        const double fi = m.g[i];
+        double c;
+        if (fi >= 1.0) {
+            c = 1.0;
+        } else {
+            double Ki;
+            if (at_floor) {
+                Ki = k_floor;
+            } else {
+                Ki = m.K(fi, true, S, (monotone && !std::isinf(k_prev)) ? k_prev : double(S), fpos_min);
+                monotone = !std::isinf(Ki) && fi * Ki <= 1.0 - fi;
+                if (monotone && Ki == k_floor) at_floor = true;
+            }
+            k_prev = Ki;
+            c = std::isinf(Ki) ? 1.0 : 1.0 - std::pow(1.0 - fi, Ki);
+        }
+        h += fi * c;
+    }
+    *hit = h;
+    return SKX_OK;
+}

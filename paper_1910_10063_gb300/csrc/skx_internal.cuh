@@ -145,6 +145,11 @@ size_t sort_scratch_bytes(int32_t N, int64_t F);
 cudaError_t launch_sort_by_count(const uint32_t *d_cnt, int32_t N, int64_t F, int32_t *d_perm, int32_t *d_rank,
                                  void *d_scratch, size_t scratch_bytes, cudaStream_t st);
 
+// Exclusive prefix sum of d_data[L] in place (3 kernels); d_block_sums needs
+// exclusive_scan_block_sums(L) entries.
+cudaError_t exclusive_scan_u32(uint32_t *d_data, uint32_t L, uint32_t *d_block_sums, cudaStream_t st);
+uint32_t exclusive_scan_block_sums(uint32_t L);
+
 cudaError_t launch_remap(const int32_t *d_rank, int32_t N, const int32_t *d_in, int32_t *d_out, int64_t F,
                          unsigned *d_err, cudaStream_t st);
 cudaError_t launch_reorder(const int32_t *d_perm, int32_t N, const void *d_in, void *d_out, int32_t row_bytes,

@@ -312,6 +312,12 @@ SortLayout sort_layout(int32_t N) {
 
 }  // namespace
 
+cudaError_t exclusive_scan_u32(uint32_t *d_data, uint32_t L, uint32_t *d_block_sums, cudaStream_t st) {
+    return exclusive_scan(d_data, L, d_block_sums, st);
+}
+
+uint32_t exclusive_scan_block_sums(uint32_t L) { return (L + kScanTile - 1) / kScanTile + 1; }
+
 size_t sort_scratch_bytes(int32_t N, int64_t F) {
     (void)F;
     return N > 0 ? sort_layout(N).total : 0;

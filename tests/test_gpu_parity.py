@@ -345,6 +345,72 @@ def test_query_copy_end_to_end(probe_data, qname):
     assert np.array_equal(got[:, 0], key) and np.array_equal(got[:, 1], pay)
 
 
+# ------------------------------------------------------------------ Q3a, Q2, maintenance
+@pytest.mark.parametrize("k", [1, 31, 32, 33, 4000, 60_000])
+def test_topk_counts_parity(probe_data, k):
+    want = oracle.topk_counts(probe_data["fk2"], k).astype(np.int64)
+    got = skx.skx_topk_counts(probe_data["d_fk2"], k)
+    assert np.array_equal(got.cpu().numpy(), want)
+    for off in (1, 3):
+        got = skx.skx_topk_counts(offset_view(probe_data["fk2"][:100_003], off), k)
+        assert np.array_equal(got.cpu().numpy(), oracle.topk_counts(probe_data["fk2"][:100_003], k).astype(np.int64))
+    assert np.array_equal(skx.skx_topk_counts(probe_data["d_fk2"][:0].contiguous(), k).cpu().numpy(), np.zeros(k))
+
+
+@pytest.mark.parametrize("c", [0, 1, 50, 100])
+def test_select_parity(probe_data, c):
+    n = probe_data["dim"].shape[0]
+    for dim, d_dim, fk, d_fk in [(probe_data["dim"], probe_data["d_dim"], probe_data["fk"], probe_data["d_fk"]),
+                                 (probe_data["dim2"], probe_data["d_dim2"], probe_data["fk2"], probe_data["d_fk2"])]:
+        bits = skx.skx_select_bitmap(d_dim, 1, c)
+        want_bits = np.packbits((dim[:, 1] < c).astype(np.uint8), bitorder="little")
+        want_bits = np.pad(want_bits, (0, bits.numel() * 4 - want_bits.size)).view(np.int32)
+        assert np.array_equal(bits.cpu().numpy(), want_bits)
+        offs, cnt = skx.skx_select(bits, n, d_fk)
+        want = oracle.select(dim, fk, 1, c)
+        assert int(cnt.item()) == want.size
+        assert np.array_equal(offs[:want.size].cpu().numpy().view(np.uint32), want)
+    # the same offsets from both layouts: the fact order is unchanged by the remap
+    assert status() == skx.SKX_OK
+
+
+def test_select_ragged_and_errors(probe_data):
+    n = probe_data["dim"].shape[0]
+    bits = skx.skx_select_bitmap(probe_data["d_dim"], 1, 50)
+    for f in (0, 1, 31, 8193):
+        offs, cnt = skx.skx_select(bits, n, probe_data["d_fk"][:f].contiguous())
+        want = oracle.select(probe_data["dim"], probe_data["fk"][:f], 1, 50)
+        assert int(cnt.item()) == want.size
+        assert np.array_equal(offs[:want.size].cpu().numpy().view(np.uint32), want)
+    bad = dev(np.array([0, n, 1], dtype=np.int32))
+    offs, cnt = skx.skx_select(bits, n, bad)
+    assert status() == skx.SKX_EKEYRANGE
+
+
+def test_index_append_and_probe():
+    n, extra = 20_000, 3_000
+    w = synth.Workload(n + extra, 400_000, 1.0, seed=13, width=16)
+    dim_all = w.dim()
+    fk_old = (w.fk() % n).astype(np.int32)              # the index is built before the new rows exist
+    idx = skx.skx_build_index(dev(fk_old), n)
+    cnt, perm, rank = oracle.build_index(fk_old, n)
+    skx.skx_index_append(idx, extra)
+    p2, r2 = oracle.index_append(perm, rank, extra)
+    assert np.array_equal(idx.perm.cpu().numpy(), p2)
+    assert np.array_equal(idx.rank.cpu().numpy(), r2)
+    assert np.array_equal(idx.counts.cpu().numpy()[n:], np.zeros(extra, np.int32))
+    # facts that reference old and new rows, remapped through the stale-but-extended index
+    fk_new = w.fk()
+    d_fk = dev(fk_new)
+    fk2 = torch.empty_like(d_fk)
+    skx.skx_remap(idx, d_fk, fk2)
+    dim2 = torch.empty((n + extra, 16), dtype=torch.int32, device=DEV)
+    skx.skx_reorder(idx, dev(dim_all), dim2)
+    got = skx.skx_probe_aggregate(dim2, fk2, dev(w.measure()), skx.Query.groupby_sum())
+    assert np.array_equal(got.cpu().numpy(), oracle.probe(dim_all, fk_new, w.measure(), nthreads=8))
+    assert status() == skx.SKX_OK
+
+
 # ------------------------------------------------------------------ batched probes
 @pytest.fixture(scope="module")
 def batch_data():
