@@ -42,6 +42,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--mode", choices=["step", "cachefit"], default="step",
+                   help="step: the timed path (default); cachefit: dimension-size sweep with 1B fact rows")
     p.add_argument("--n", type=int, default=20_000_000, help="dimension rows")
     p.add_argument("--f", type=int, default=500_000_000, help="fact rows")
     p.add_argument("--s", type=float, default=1.0, help="Zipf exponent of the timed step")
@@ -383,6 +385,30 @@ def run_ours(a, rank, world, local_rank):
                                "frac_hbm": round(gbs / peak, 4),
                                "tuning": {k: tun.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
                                                                          "hot_keys", "lane_keys")}}
+            # other operators on the same column: Q3a top-4000 vs the full Q3 count, Q2 selection
+            def t_ms(fn, reps=5):
+                out_ms = []
+                for _ in range(reps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                    e1.synchronize()
+                    out_ms.append(e0.elapsed_time(e1))
+                return round(statistics.median(out_ms), 4)
+            cnt_buf = torch.empty(a.n, dtype=torch.int32, device=dev)
+            top = torch.empty(4000, dtype=torch.int64, device=dev)
+            entry["q3_full_count_ms"] = t_ms(lambda: skx.skx_count(fk2, a.n, cnt_buf))
+            entry["q3a_top4000_ms"] = t_ms(lambda: skx.skx_topk_counts(fk2, 4000, out=top))
+            entry["speedup_top4000_vs_full_count"] = round(entry["q3_full_count_ms"] / entry["q3a_top4000_ms"], 2)
+            bits_p = skx.skx_select_bitmap(w.dim, 1, 50)
+            bits_r = skx.skx_select_bitmap(dim2, 1, 50)
+            offs = torch.empty(a.f, dtype=torch.int32, device=dev)
+            cnt1 = torch.empty(1, dtype=torch.int64, device=dev)
+            entry["q2_select_plain_ms"] = t_ms(lambda: skx.skx_select(bits_p, a.n, fk_s, offs, cnt1))
+            entry["q2_select_remapped_ms"] = t_ms(lambda: skx.skx_select(bits_r, a.n, fk2, offs, cnt1))
+            del offs, cnt_buf
             entry["speedup_remapped_vs_plain"] = round(entry["plain"]["ms"] / entry["remapped"]["ms"], 3)
             entry["speedup_columns16"] = round(entry["plain_columns16"]["ms"] / entry["remapped_columns16"]["ms"], 3)
             entry["speedup_query8"] = round(entry["plain_query8"]["ms"] / entry["remapped_query8"]["ms"], 3)
@@ -397,6 +423,11 @@ def run_ours(a, rank, world, local_rank):
         st = skx.skx_stream_status()
         if st != skx.SKX_OK:
             raise RuntimeError(f"device status {st} during the sweep")
+
+    # ---------------- Section III-C cache model: predicted L2 hit rate of the gathers
+    cache_model = None
+    if rank == 0:
+        cache_model = predict_l2(a, w)
 
     # ---------------- batched queries: 512 uneven fact batches in one persistent launch
     batch = None
@@ -461,10 +492,123 @@ def run_ours(a, rank, world, local_rank):
         "probe": {"remapped_p50_ms": round(statistics.median(probe_lat), 4) if probe_lat else None,
                   "remapped_p99_ms": round(float(np.percentile(probe_lat, 99)), 4) if probe_lat else None,
                   "sweep": sweep},
-        "batch": batch, "serving": serving,
+        "cache_model": cache_model, "batch": batch, "serving": serving,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
     }
     return line
+
+
+def predict_l2(a, w, line_bytes=128):
+    """The Section III-C model for the probe's dimension gathers on both layouts:
+    cache lines of 128 bytes over 64-byte rows, access frequencies from the Zipf
+    pmf (rank r) -- remapped: row r is rank r; plain: row v is rank rank_of(v)."""
+    import paper_1910_10063_gb300 as skx
+    from paper_1910_10063_gb300 import synth
+    import torch
+    cdf = synth.zipf_cdf(a.n, a.s)
+    p_rank = np.diff(np.concatenate([[0.0], cdf]))
+    rows_per_line = max(1, line_bytes // (a.width * 4))
+    L2 = torch.cuda.get_device_properties(0).L2_cache_size
+    S = L2 // line_bytes
+    nl = (a.n + rows_per_line - 1) // rows_per_line
+
+    def lines(p_row):
+        pad = np.zeros(nl * rows_per_line)
+        pad[:a.n] = p_row
+        return pad.reshape(nl, rows_per_line).sum(axis=1)
+    rank_of_id = np.empty(a.n, dtype=np.int64)
+    rank_of_id[w.r2id_host] = np.arange(a.n)
+    t0 = time.perf_counter()
+    hit_r = skx.skx_cache_hit_rate(lines(p_rank), S)
+    hit_p = skx.skx_cache_hit_rate(lines(p_rank[rank_of_id]), S)
+    return {"model": "Section III-C stack-distance model, LRU of the whole L2", "l2_bytes": int(L2),
+            "line_bytes": line_bytes, "lines_in_cache": int(S), "dimension_lines": int(nl),
+            "predicted_hit_remapped": round(hit_r, 4), "predicted_hit_plain": round(hit_p, 4),
+            "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def run_cachefit(a):
+    """Dimension-size sweep with 1B Zipf(1.0) fact rows: index build, remap, reorder, plain and
+    remapped probes; plus the drifting-popularity variant (10% of ranks re-shuffled): the stale
+    index vs a rebuild."""
+    import torch
+    import paper_1910_10063_gb300 as skx
+    from paper_1910_10063_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    q = skx.Query.groupby_sum()
+    F = 1_000_000_000
+
+    def timed(fn, reps=3):
+        best = 1e30
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            e1.synchronize()
+            if hasattr(r, "close"):
+                r.close()
+            best = min(best, e0.elapsed_time(e1))
+        return round(best, 3)
+
+    rows = []
+    sizes = [1, 2, 4, 8, 16, 32, 64, 128, 200]
+    measure = synth.measure_device(a.seed, F, device=dev)
+    for nm in sizes:
+        n = nm * 1_000_000
+        w = synth.DeviceWorkload(n, F, 1.0, seed=a.seed, width=a.width, device=dev, with_measure=False)
+        fk2 = torch.empty_like(w.fk)
+        dim2 = torch.empty_like(w.dim)
+        t_build = timed(lambda: skx.skx_build_index(w.fk, n))
+        idx = skx.skx_build_index(w.fk, n)
+        t_remap = timed(lambda: skx.skx_remap(idx, w.fk, fk2))
+        t_reorder = timed(lambda: skx.skx_reorder(idx, w.dim, dim2))
+        tp, _ = skx.skx_probe_autotune(w.dim, w.fk, measure, q, remapped=False)
+        tr, _ = skx.skx_probe_autotune(dim2, fk2, measure, q, remapped=True)
+        t_plain = timed(lambda: skx.skx_probe_aggregate(w.dim, w.fk, measure, q, tuning=tp))
+        t_rem = timed(lambda: skx.skx_probe_aggregate(dim2, fk2, measure, q, tuning=tr))
+        a_ = skx.skx_probe_aggregate(w.dim, w.fk, measure, q, tuning=tp).cpu()
+        b_ = skx.skx_probe_aggregate(dim2, fk2, measure, q, tuning=tr).cpu()
+        rows.append({"N": n, "table_bytes": n * a.width * 4, "build_ms": t_build, "remap_ms": t_remap,
+                     "reorder_ms": t_reorder, "probe_plain_ms": t_plain, "probe_remapped_ms": t_rem,
+                     "speedup": round(t_plain / t_rem, 3), "identical": bool(torch.equal(a_, b_)),
+                     "remapped_tuning_hot_keys": tr.hot_keys})
+        if nm == 64:
+            # drift: 10% of the ranks re-shuffled; the old index stays in use vs a rebuild
+            r2d = synth.drift_rank_to_id(w.r2id_host, a.seed, 0.1)
+            wd = synth.DeviceWorkload(n, F, 1.0, seed=a.seed + 1, width=a.width, device=dev, r2id=r2d,
+                                      with_measure=False, with_dim=False)
+            fks = torch.empty_like(wd.fk)
+            skx.skx_remap(idx, wd.fk, fks)  # stale recode
+            t_stale = timed(lambda: skx.skx_probe_aggregate(dim2, fks, measure, q, tuning=tr))
+            want = skx.skx_probe_aggregate(w.dim, wd.fk, measure, q, tuning=tp).cpu()
+            stale_ok = torch.equal(skx.skx_probe_aggregate(dim2, fks, measure, q, tuning=tr).cpu(), want)
+            idx2 = skx.skx_build_index(wd.fk, n)
+            dim3 = torch.empty_like(dim2)
+
+            def rebuild():
+                i2 = skx.skx_build_index(wd.fk, n)
+                skx.skx_remap(i2, wd.fk, fks)
+                skx.skx_reorder(i2, w.dim, dim3)
+                return i2
+            t_rebuild = timed(rebuild)
+            skx.skx_remap(idx2, wd.fk, fks)
+            skx.skx_reorder(idx2, w.dim, dim3)
+            t_fresh = timed(lambda: skx.skx_probe_aggregate(dim3, fks, measure, q, tuning=tr))
+            fresh_ok = torch.equal(skx.skx_probe_aggregate(dim3, fks, measure, q, tuning=tr).cpu(), want)
+            rows[-1]["drift"] = {"reshuffled_ranks": 0.1, "stale_probe_ms": t_stale, "fresh_probe_ms": t_fresh,
+                                 "rebuild_ms": t_rebuild, "both_exact": bool(stale_ok and fresh_ok)}
+            idx2.close()
+            del wd, fks, dim3
+        idx.close()
+        del w, fk2, dim2
+        torch.cuda.empty_cache()
+    st = skx.skx_stream_status()
+    return {"mode": "cachefit", "F": F, "zipf_s": 1.0, "row_bytes": a.width * 4, "status": st, "rows": rows}
 
 
 def batch_workload(a, w, dev, nq, seed=1):
@@ -716,6 +860,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if a.impl == "reference":
         line = run_reference(a, rank, world)
+    elif a.mode == "cachefit":
+        line = run_cachefit(a) if rank == 0 else None
     else:
         line = run_ours(a, rank, world, local_rank)
     if line is not None:
