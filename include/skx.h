@@ -112,6 +112,36 @@ skx_status skx_build_index_from_counts(const uint32_t *d_counts, int32_t N, int6
                                        skx_index **out);
 
 /*
+ * The count of skx_count with the algorithm chosen by the caller (both give
+ * identical counts; the choice only moves time between kernels):
+ *   SKX_COUNT_AUTO         what skx_count and skx_build_index use.  For
+ *                          2^24 <= N <= 2^26 and F >= 2^28 (when the
+ *                          partitioned count's scratch can be allocated) a
+ *                          kernel samples 8192 keys of d_fk and picks on the
+ *                          device, without a host synchronisation: the single
+ *                          pass when most sampled keys repeat in the sample
+ *                          (heavy skew), else the partitioned count.  Smaller
+ *                          inputs take the single pass;
+ *   SKX_COUNT_SINGLE_PASS  one pass over d_fk, a per-CTA shared-memory cache
+ *                          of hot ids and L2 atomics for the rest;
+ *   SKX_COUNT_PARTITIONED  radix partition of the keys by 2^15-id buckets
+ *                          (two passes over d_fk, 2 bytes per key of scratch
+ *                          written and read back) and a shared-memory count
+ *                          per bucket; no random global access.  Needs
+ *                          N <= 2^26; allocates 2 * F bytes (plus a few MB)
+ *                          of stream-ordered scratch.
+ * Errors: as skx_count; SKX_EINVAL for an unknown method; SKX_ENOTSUP when
+ * SKX_COUNT_PARTITIONED is asked for with N > 2^26.
+ */
+typedef enum {
+    SKX_COUNT_AUTO = 0,
+    SKX_COUNT_SINGLE_PASS = 1,
+    SKX_COUNT_PARTITIONED = 2
+} skx_count_method;
+skx_status skx_count_ex(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_counts, int32_t method,
+                        void *stream);
+
+/*
  * Allocation-free variant of the frequency sort, for callers that must not
  * allocate device memory when they build the order -- for example because a
  * framework's caching allocator already holds almost all of HBM, because an

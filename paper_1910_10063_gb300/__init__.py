@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(PKG, "libskx.so")
 SKX_OK, SKX_EINVAL, SKX_ENOMEM, SKX_EKEYRANGE, SKX_EGROUPRANGE = 0, 1, 2, 3, 4
 SKX_ECUDA, SKX_ETIMEOUT, SKX_EBUSY, SKX_ENOTSUP = 5, 6, 7, 8
 SKX_AGG_COUNT, SKX_AGG_SUM, SKX_AGG_GROUPBY_SUM = 0, 1, 2
+SKX_COUNT_AUTO, SKX_COUNT_SINGLE_PASS, SKX_COUNT_PARTITIONED = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -118,6 +119,7 @@ def lib():
             L.skx_stream_status.argtypes = [P]; L.skx_stream_status.restype = st
             L.skx_build_index.argtypes = [P, i64, i32, P, ctypes.POINTER(P)]; L.skx_build_index.restype = st
             L.skx_count.argtypes = [P, i64, i32, P, P]; L.skx_count.restype = st
+            L.skx_count_ex.argtypes = [P, i64, i32, P, i32, P]; L.skx_count_ex.restype = st
             L.skx_build_index_from_counts.argtypes = [P, i32, i64, P, ctypes.POINTER(P)]
             L.skx_build_index_from_counts.restype = st
             L.skx_sort_by_count_noalloc.argtypes = [P, i32, i64, P, P, P]
@@ -289,6 +291,16 @@ def skx_count(fk, n: int, counts=None, stream=None):
         counts = torch.empty(n, dtype=torch.int32, device=fk.device)
     _check(lib().skx_count(_dptr(fk, "fk", torch.int32), fk.numel(), int(n), _dptr(counts, "counts", torch.int32),
                            _stream(stream)), "skx_count")
+    return counts
+
+
+def skx_count_ex(fk, n: int, method: int, counts=None, stream=None):
+    """Q3 count with the algorithm chosen (SKX_COUNT_AUTO / _SINGLE_PASS / _PARTITIONED)."""
+    import torch
+    if counts is None:
+        counts = torch.empty(n, dtype=torch.int32, device=fk.device)
+    _check(lib().skx_count_ex(_dptr(fk, "fk", torch.int32), fk.numel(), int(n), _dptr(counts, "counts", torch.int32),
+                              int(method), _stream(stream)), "skx_count_ex")
     return counts
 
 

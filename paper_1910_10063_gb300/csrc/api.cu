@@ -185,8 +185,20 @@ skx_status skx_count(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_coun
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned *err = device_error_word();
     if (!err) return SKX_ENOMEM;
-    SKX_CUDA_TRY(cudaMemsetAsync(d_counts, 0, size_t(N) * 4, st));
-    SKX_CUDA_TRY(launch_histogram(d_fk, F, N, d_counts, err, st));
+    SKX_CUDA_TRY(launch_count(d_fk, F, N, d_counts, err, SKX_COUNT_AUTO, st));
+    return SKX_OK;
+}
+
+skx_status skx_count_ex(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_counts, int32_t method,
+                        void *stream) {
+    if (N < 1 || F < 0 || F >= (int64_t(1) << 32) || (F > 0 && !d_fk) || !d_counts || !valid_stream_ptrs(d_fk) ||
+        !valid_stream_ptrs(d_counts) || method < SKX_COUNT_AUTO || method > SKX_COUNT_PARTITIONED)
+        return SKX_EINVAL;
+    if (method == SKX_COUNT_PARTITIONED && !histogram_partitioned_fits(N, F > 0 ? F : 1)) return SKX_ENOTSUP;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    SKX_CUDA_TRY(launch_count(d_fk, F, N, d_counts, err, method, st));
     return SKX_OK;
 }
 
@@ -198,9 +210,7 @@ skx_status skx_build_index(const int32_t *d_fk, int64_t F, int32_t N, void *stre
     unsigned *err = device_error_word();
     if (!err) return SKX_ENOMEM;
     return make_index(N, F, st, out, [&](uint32_t *counts) {
-        cudaError_t e = cudaMemsetAsync(counts, 0, size_t(N) * 4, st);
-        if (e == cudaSuccess) e = launch_histogram(d_fk, F, N, counts, err, st);
-        return e;
+        return launch_count(d_fk, F, N, counts, err, SKX_COUNT_AUTO, st);
     });
 }
 

@@ -53,7 +53,8 @@ __device__ __forceinline__ void count_key(int32_t key, bool valid, int32_t N, ui
 
 __global__ void __launch_bounds__(kHistBlock)
     k_histogram(const int32_t *__restrict__ fk, int64_t F, int64_t head, int32_t N, uint32_t *__restrict__ cnt,
-                unsigned *err) {
+                unsigned *err, const uint32_t *skip_if_set) {
+    if (skip_if_set && *skip_if_set) return;  // the partitioned count was chosen on the device
     __shared__ int32_t s_key[kSlots];
     __shared__ uint32_t s_cnt[kSlots];
     for (int i = threadIdx.x; i < kSlots; i += kHistBlock) {
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kHistBlock)
 }  // namespace
 
 cudaError_t launch_histogram(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_cnt, unsigned *d_err,
-                             cudaStream_t st) {
+                             cudaStream_t st, const uint32_t *skip_if_set) {
     if (F <= 0) return cudaSuccess;
     const int64_t mis = (int64_t)((reinterpret_cast<uintptr_t>(d_fk) & 15u) >> 2);
     const int64_t head = mis ? (F < 4 - mis ? F : 4 - mis) : 0;
@@ -118,9 +119,39 @@ cudaError_t launch_histogram(const int32_t *d_fk, int64_t F, int32_t N, uint32_t
     int64_t want = (nvec + 32 * kHistUnroll * (kHistBlock / 32) - 1) / (32 * kHistUnroll * (kHistBlock / 32));
     int64_t cap = (int64_t)sms * (2048 / kHistBlock);
     int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
-    k_histogram<<<grid, kHistBlock, 0, st>>>(d_fk, F, head, N, d_cnt, d_err);
+    k_histogram<<<grid, kHistBlock, 0, st>>>(d_fk, F, head, N, d_cnt, d_err, skip_if_set);
     note_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_count(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_cnt, unsigned *d_err, int method,
+                         cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(d_cnt, 0, size_t(N) * 4, st);
+    if (e != cudaSuccess || F <= 0) return e;
+    bool part = method == SKX_COUNT_PARTITIONED;
+    if (method == SKX_COUNT_AUTO)
+        part = N >= (1 << 24) && F >= (int64_t(1) << 28) && histogram_partitioned_fits(N, F);
+    if (!part) return launch_histogram(d_fk, F, N, d_cnt, d_err, st);
+    const size_t sb = histogram_partitioned_scratch(N, F);
+    void *scratch = nullptr;
+    e = cudaMallocAsync(&scratch, sb, st);
+    if (e != cudaSuccess) {
+        if (method != SKX_COUNT_AUTO) return e;
+        (void)cudaGetLastError();
+        return launch_histogram(d_fk, F, N, d_cnt, d_err, st);
+    }
+    if (method == SKX_COUNT_AUTO) {
+        // a sample of the column decides on the device which count runs; the
+        // other one's kernels return at once
+        const uint32_t *flag = nullptr;
+        e = launch_count_choice(d_fk, F, N, scratch, sb, &flag, st);
+        if (e == cudaSuccess) e = launch_histogram(d_fk, F, N, d_cnt, d_err, st, flag);
+        if (e == cudaSuccess) e = launch_histogram_partitioned(d_fk, F, N, d_cnt, d_err, scratch, sb, st, flag);
+    } else {
+        e = launch_histogram_partitioned(d_fk, F, N, d_cnt, d_err, scratch, sb, st);
+    }
+    const cudaError_t f = cudaFreeAsync(scratch, st);
+    return e != cudaSuccess ? e : f;
 }
 
 }  // namespace skx

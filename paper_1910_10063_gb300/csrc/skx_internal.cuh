@@ -124,9 +124,32 @@ __device__ __forceinline__ void raise_error(unsigned *err, unsigned bit) {
 // -------------------------------------------------------------- internal entry points
 // (launchers shared between the C-ABI implementation and the batch/serving paths)
 
-// Histogram of keys[F] into cnt[N] (cnt must be zeroed by the caller).
+// Histogram of keys[F] into cnt[N] (cnt must be zeroed by the caller).  With
+// skip_if_set, the kernel returns at once when that device word is nonzero.
 cudaError_t launch_histogram(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_cnt, unsigned *d_err,
-                             cudaStream_t st);
+                             cudaStream_t st, const uint32_t *skip_if_set = nullptr);
+
+// The partitioned count (histogram_part.cu): same contract as launch_histogram
+// (cnt zeroed by the caller), with caller-provided scratch of at least
+// histogram_partitioned_scratch(N, F) bytes (16-byte aligned).
+// With run_if_set, its kernels return at once when that device word is zero.
+bool histogram_partitioned_fits(int32_t N, int64_t F);
+size_t histogram_partitioned_scratch(int32_t N, int64_t F);
+cudaError_t launch_histogram_partitioned(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_cnt, unsigned *d_err,
+                                         void *d_scratch, size_t scratch_bytes, cudaStream_t st,
+                                         const uint32_t *run_if_set = nullptr);
+// Samples the column and sets a device word (inside the partitioned count's
+// scratch; *flag points to it) to 1 when the partitioned count should run, 0
+// when the single pass should: the single pass wins when most keys belong to
+// ids that its per-CTA cache holds.
+cudaError_t launch_count_choice(const int32_t *d_fk, int64_t F, int32_t N, void *d_scratch, size_t scratch_bytes,
+                                const uint32_t **flag, cudaStream_t st);
+
+// The count the entry points use (method: skx_count_method).  Zeroes cnt,
+// allocates the partitioned count's scratch on st and frees it there; in
+// SKX_COUNT_AUTO a failed allocation falls back to the single pass.
+cudaError_t launch_count(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_cnt, unsigned *d_err, int method,
+                         cudaStream_t st);
 
 // Scratch bytes the frequency sort needs for n ids: four 4-byte arrays of n
 // (keys and ids, ping-pong), the per-tile digit counts (256 per 4096-id tile),
@@ -146,8 +169,10 @@ cudaError_t launch_sort_by_count(const uint32_t *d_cnt, int32_t N, int64_t F, in
                                  void *d_scratch, size_t scratch_bytes, cudaStream_t st);
 
 // Exclusive prefix sum of d_data[L] in place (3 kernels); d_block_sums needs
-// exclusive_scan_block_sums(L) entries.
-cudaError_t exclusive_scan_u32(uint32_t *d_data, uint32_t L, uint32_t *d_block_sums, cudaStream_t st);
+// exclusive_scan_block_sums(L) entries.  With run_if_set, the kernels return
+// at once when that device word is zero.
+cudaError_t exclusive_scan_u32(uint32_t *d_data, uint32_t L, uint32_t *d_block_sums, cudaStream_t st,
+                               const uint32_t *run_if_set = nullptr);
 uint32_t exclusive_scan_block_sums(uint32_t L);
 
 cudaError_t launch_remap(const int32_t *d_rank, int32_t N, const int32_t *d_in, int32_t *d_out, int64_t F,

@@ -142,7 +142,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 }
 
 __global__ void __launch_bounds__(kSortBlock) k_scan_reduce(const uint32_t *__restrict__ data, uint32_t L,
-                                                           uint32_t *__restrict__ block_sums) {
+                                                           uint32_t *__restrict__ block_sums, const uint32_t *go) {
+    if (go && !*go) return;
     __shared__ uint32_t s_warp[33];
     const uint32_t base = blockIdx.x * kScanTile;
     uint32_t s = 0;
@@ -156,7 +157,8 @@ __global__ void __launch_bounds__(kSortBlock) k_scan_reduce(const uint32_t *__re
     if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_single(uint32_t *__restrict__ data, uint32_t L) {
+__global__ void __launch_bounds__(1024) k_scan_single(uint32_t *__restrict__ data, uint32_t L, const uint32_t *go) {
+    if (go && !*go) return;
     __shared__ uint32_t s_warp[33];
     uint32_t carry = 0;
     for (uint32_t base = 0; base < L; base += blockDim.x) {
@@ -170,7 +172,8 @@ __global__ void __launch_bounds__(1024) k_scan_single(uint32_t *__restrict__ dat
 }
 
 __global__ void __launch_bounds__(kSortBlock) k_scan_apply(uint32_t *__restrict__ data, uint32_t L,
-                                                          const uint32_t *__restrict__ block_sums) {
+                                                          const uint32_t *__restrict__ block_sums, const uint32_t *go) {
+    if (go && !*go) return;
     __shared__ uint32_t s_warp[33];
     // thread t owns kScanItems consecutive elements
     const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
@@ -190,11 +193,12 @@ __global__ void __launch_bounds__(kSortBlock) k_scan_apply(uint32_t *__restrict_
     }
 }
 
-cudaError_t exclusive_scan(uint32_t *d_data, uint32_t L, uint32_t *d_block_sums, cudaStream_t st) {
+cudaError_t exclusive_scan(uint32_t *d_data, uint32_t L, uint32_t *d_block_sums, cudaStream_t st,
+                           const uint32_t *go = nullptr) {
     const uint32_t nb = (L + kScanTile - 1) / kScanTile;
-    k_scan_reduce<<<nb, kSortBlock, 0, st>>>(d_data, L, d_block_sums);
-    k_scan_single<<<1, 1024, 0, st>>>(d_block_sums, nb);
-    k_scan_apply<<<nb, kSortBlock, 0, st>>>(d_data, L, d_block_sums);
+    k_scan_reduce<<<nb, kSortBlock, 0, st>>>(d_data, L, d_block_sums, go);
+    k_scan_single<<<1, 1024, 0, st>>>(d_block_sums, nb, go);
+    k_scan_apply<<<nb, kSortBlock, 0, st>>>(d_data, L, d_block_sums, go);
     note_launches(3);
     return cudaGetLastError();
 }
@@ -312,8 +316,9 @@ SortLayout sort_layout(int32_t N) {
 
 }  // namespace
 
-cudaError_t exclusive_scan_u32(uint32_t *d_data, uint32_t L, uint32_t *d_block_sums, cudaStream_t st) {
-    return exclusive_scan(d_data, L, d_block_sums, st);
+cudaError_t exclusive_scan_u32(uint32_t *d_data, uint32_t L, uint32_t *d_block_sums, cudaStream_t st,
+                               const uint32_t *run_if_set) {
+    return exclusive_scan(d_data, L, d_block_sums, st, run_if_set);
 }
 
 uint32_t exclusive_scan_block_sums(uint32_t L) { return (L + kScanTile - 1) / kScanTile + 1; }

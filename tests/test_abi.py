@@ -64,6 +64,11 @@ def test_argument_errors_without_gpu():
     assert L.skx_probe_aggregate(ctypes.c_void_p(16), 10, 16, ctypes.c_void_p(16), ctypes.c_void_p(16), 10,
                                  ctypes.byref(q), ctypes.c_void_p(16), None, None) == skx.SKX_EINVAL
     assert L.skx_remap(None, None, None, 5, None) == skx.SKX_EINVAL
+    P = ctypes.c_void_p
+    assert L.skx_count_ex(P(16), 10, 5, P(16), 7, None) == skx.SKX_EINVAL
+    assert L.skx_count_ex(P(16), 10, 5, P(16), -1, None) == skx.SKX_EINVAL
+    assert L.skx_count_ex(P(16), 1 << 32, 5, P(16), skx.SKX_COUNT_AUTO, None) == skx.SKX_EINVAL
+    assert L.skx_count_ex(P(16), 10, (1 << 26) + 1, P(16), skx.SKX_COUNT_PARTITIONED, None) == skx.SKX_ENOTSUP
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

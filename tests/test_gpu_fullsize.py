@@ -1,7 +1,7 @@
 """Parity at the full configured sizes, with the launch configurations bench.py
 times (autotuned probe, whole-row reorder, batched plan, serving loop).
 
-* 20M x 64-byte rows, 500M-row FK column: counts, perm, rank, remap and
+* 20M x 64-byte rows, 500M-row FK column: counts (both count algorithms), perm, rank, remap and
   reorder compared with the oracle element by element, and the probe result at
   Zipf s in {0, 0.5, 1.0, 1.5} on the remapped layout compared with the oracle
   on the original layout.
@@ -54,6 +54,10 @@ def test_large_build_remap_reorder_exact(large):
     assert np.array_equal(idx.counts.cpu().numpy().view(np.uint32).astype(np.uint64), cnt)
     assert np.array_equal(idx.perm.cpu().numpy(), perm)
     assert np.array_equal(idx.rank.cpu().numpy(), rank)
+    for method in (skx.SKX_COUNT_SINGLE_PASS, skx.SKX_COUNT_PARTITIONED):  # both count algorithms
+        c = skx.skx_count_ex(w.fk, N1, method)
+        assert np.array_equal(c.cpu().numpy().view(np.uint32).astype(np.uint64), cnt)
+        del c
     assert np.array_equal(fk2.cpu().numpy(), oracle.remap(rank, fk))
     assert np.array_equal(dim2.cpu().numpy(), oracle.reorder(perm, w.dim.cpu().numpy()))
     idx.close()

@@ -93,6 +93,88 @@ def test_build_index_unaligned(offset):
     assert np.array_equal(idx.counts.cpu().numpy().view(np.uint32).astype(np.uint64), cnt)
 
 
+# ------------------------------------------------------------------ count methods
+METHODS = [skx.SKX_COUNT_SINGLE_PASS, skx.SKX_COUNT_PARTITIONED]
+
+
+def _counts_np(c):
+    return c.cpu().numpy().view(np.uint32).astype(np.uint64)
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("n,f,s,seed,offset", [
+    (1, 9, 1.0, 0, 0),
+    (8, 10, 0.0, 1, 3),               # tiny: head and tail only, no full vector in most CTAs
+    (32768, 100_001, 1.0, 2, 1),      # exactly one bucket of 2^15 ids
+    (100_003, 3_000_001, 1.0, 3, 2),  # 4 buckets, the last ragged; many phase-C tiles
+    (2_500_000, 6_000_007, 1.0, 4, 0),  # the size-based choice takes the partitioned count
+    (300_000, 4_000_000, 0.0, 5, 1),  # uniform
+    (70_000, 5_000_000, 1.5, 6, 0),   # heavy skew: hot ids' buckets span several 2^20-key chunks
+])
+def test_count_methods_parity(method, n, f, s, seed, offset):
+    w = synth.Workload(n, f, s, seed=seed, width=4)
+    fk = w.fk()
+    c = skx.skx_count_ex(offset_view(fk, offset), n, method)
+    assert status() == skx.SKX_OK
+    assert np.array_equal(_counts_np(c), oracle.histogram(fk, n))
+
+
+@pytest.mark.parametrize("s", [1.0, 1.5])
+def test_count_auto_choice_parity(s):
+    """Sizes where the automatic count samples the column and picks an
+    algorithm on the device (s = 1.5: the single pass; s = 1.0: partitioned)."""
+    n, f = 1 << 24, (1 << 28) + 5
+    w = synth.DeviceWorkload(n, f, s, seed=12, width=1, device=DEV, with_measure=False, with_dim=False)
+    expect = oracle.histogram(w.fk.cpu().numpy(), n)
+    c = skx.skx_count(w.fk, n)
+    assert status() == skx.SKX_OK
+    assert np.array_equal(_counts_np(c), expect)
+    del w, c
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_count_methods_skewed_layouts(method):
+    """Hot ids packed into bucket 0 (same-address shared atomics in every
+    phase), one id holding every key (one bucket split into several chunks),
+    and ids that leave most buckets empty."""
+    rng = np.random.default_rng(23)
+    n = 1_000_000
+    cdf = synth.zipf_cdf(n, 1.0)
+    ident = np.arange(n, dtype=np.int32)  # rank r -> id r: popularity follows the id order
+    fk_ident = synth.zipf_fk_host(cdf, ident, 5, 0, 4_000_003)
+    fk_one = np.full(3_000_005, 777_777, dtype=np.int32)
+    fk_sparse = rng.integers(0, 1000, 2_000_000).astype(np.int32) * 997
+    for fk in (fk_ident, fk_one, fk_sparse):
+        c = skx.skx_count_ex(dev(fk), n, method)
+        assert status() == skx.SKX_OK
+        assert np.array_equal(_counts_np(c), oracle.histogram(fk, n))
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_count_methods_key_range(method):
+    n = 100_000
+    fk = synth.Workload(n, 500_001, 1.0, seed=8).fk()
+    bad = fk.copy()
+    bad[[0, 12345, 500_000]] = [n, -1, 2**31 - 1]
+    c = skx.skx_count_ex(dev(bad), n, method)
+    assert status() == skx.SKX_EKEYRANGE
+    keep = np.ones(bad.size, dtype=bool)
+    keep[[0, 12345, 500_000]] = False
+    assert np.array_equal(_counts_np(c), oracle.histogram(bad[keep], n))
+
+
+def test_count_method_errors():
+    fk = dev(np.zeros(16, dtype=np.int32))
+    with pytest.raises(skx.SkxError) as e:
+        skx.skx_count_ex(fk, 10, 7)
+    assert e.value.status == skx.SKX_EINVAL
+    with pytest.raises(skx.SkxError) as e:
+        skx.skx_count_ex(fk, (1 << 26) + 1, skx.SKX_COUNT_PARTITIONED,
+                         counts=torch.empty(1, dtype=torch.int32, device=DEV))
+    assert e.value.status == skx.SKX_ENOTSUP
+
+
 def test_sort_heavy_light_split_cases():
     """Counts >= 255 take the multi-pass path, smaller ones the single clamped pass."""
     rng = np.random.default_rng(17)
