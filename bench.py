@@ -97,16 +97,33 @@ def source_sha(path):
 
 
 def ncu_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged.
+    A key "a+b+c" sums the kernels of a stage that runs several."""
     try:
         with open(TRAFFIC_PATH) as fh:
-            rec = json.load(fh)[kernel_key]
-        src = os.path.join(ROOT, rec["source"])
-        if source_sha(src) != rec["source_sha"]:
-            return None
-        return rec["bytes_per_launch"]
+            table = json.load(fh)
+        total = 0
+        for k in kernel_key.split("+"):
+            rec = table[k]
+            if source_sha(os.path.join(ROOT, rec["source"])) != rec["source_sha"]:
+                return None
+            total += rec["bytes_per_launch"]
+        return total
     except Exception:
         return None
+
+
+def count_kernels(fk, n, f):
+    """Kernels the library's automatic count runs on this column: it samples 8192 keys at stride
+    f // 8192 on the device and takes the partitioned count (2^24 <= n <= 2^26, f >= 2^28) unless
+    60 % or more of the sampled keys repeat in the sample.  The same rule, evaluated here, only
+    labels the stage in the report."""
+    if not (2 ** 24 <= n <= 2 ** 26 and f >= 2 ** 28):
+        return "k_histogram"
+    sample = fk[:: f // 8192][:8192].cpu().numpy()
+    _, c = np.unique(sample, return_counts=True)
+    dup = float(c[c >= 2].sum()) / max(sample.size, 1)
+    return "k_histogram" if dup >= 0.6 else "k_part_count+k_part_scatter+k_part_hist"
 
 
 class ClockSampler:
@@ -302,16 +319,13 @@ def run_ours(a, rank, world, local_rank):
     row_b = a.width * 4
     alg = {"count": 4 * a.f + 4 * a.n, "sort": 12 * a.n, "remap": 8 * a.f + 4 * a.n,
            "reorder": 2 * row_b * a.n + 4 * a.n, "probe": 8 * a.f + 16 * D}
-    kernel_of = {"count": "k_histogram", "sort": "k_radix_*", "remap": "k_remap", "reorder": "k_reorder",
+    kernel_of = {"count": count_kernels(w.fk, a.n, a.f), "sort": "k_radix_*", "remap": "k_remap", "reorder": "k_reorder",
                  "probe": "k_probe"}
-    src_of = {"count": "paper_1910_10063_gb300/csrc/histogram.cu", "sort": "paper_1910_10063_gb300/csrc/sort.cu",
-              "remap": "paper_1910_10063_gb300/csrc/remap.cu", "reorder": "paper_1910_10063_gb300/csrc/remap.cu",
-              "probe": "paper_1910_10063_gb300/csrc/probe.cu"}
     stage_avg = {s: statistics.mean(v) for s, v in stage_ms.items()}
     stage_rep = {s: {"ms": round(stage_avg[s], 4), "alg_bytes": int(alg[s]),
                      "gbs": round(alg[s] / (stage_avg[s] * 1e-3) / 1e9, 1),
                      "frac": round(alg[s] / (stage_avg[s] * 1e-3) / 1e9 / peak, 4),
-                     "kernel": kernel_of[s]} for s in stages}
+                     "kernel": kernel_of[s], "dram_bytes": ncu_traffic(kernel_of[s])} for s in stages}
     dom = max(stages, key=lambda s: stage_avg[s])
     achieved = alg[dom] / (stage_avg[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kernel_of[dom], "stage": dom, "achieved": round(achieved, 1),
