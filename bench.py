@@ -115,10 +115,10 @@ def ncu_traffic(kernel_key):
 
 def count_kernels(fk, n, f):
     """Kernels the library's automatic count runs on this column: it samples 8192 keys at stride
-    f // 8192 on the device and takes the partitioned count (2^24 <= n <= 2^26, f >= 2^28) unless
+    f // 8192 on the device and takes the partitioned count (2^24 <= n <= 2^28, f >= 2^28) unless
     60 % or more of the sampled keys repeat in the sample.  The same rule, evaluated here, only
     labels the stage in the report."""
-    if not (2 ** 24 <= n <= 2 ** 26 and f >= 2 ** 28):
+    if not (2 ** 24 <= n <= 2 ** 28 and f >= 2 ** 28):
         return "k_histogram"
     sample = fk[:: f // 8192][:8192].cpu().numpy()
     _, c = np.unique(sample, return_counts=True)

@@ -115,7 +115,7 @@ skx_status skx_build_index_from_counts(const uint32_t *d_counts, int32_t N, int6
  * The count of skx_count with the algorithm chosen by the caller (both give
  * identical counts; the choice only moves time between kernels):
  *   SKX_COUNT_AUTO         what skx_count and skx_build_index use.  For
- *                          2^24 <= N <= 2^26 and F >= 2^28 (when the
+ *                          2^24 <= N <= 2^28 and F >= 2^28 (when the
  *                          partitioned count's scratch can be allocated) a
  *                          kernel samples 8192 keys of d_fk and picks on the
  *                          device, without a host synchronisation: the single
@@ -128,10 +128,10 @@ skx_status skx_build_index_from_counts(const uint32_t *d_counts, int32_t N, int6
  *                          (two passes over d_fk, 2 bytes per key of scratch
  *                          written and read back) and a shared-memory count
  *                          per bucket; no random global access.  Needs
- *                          N <= 2^26; allocates 2 * F bytes (plus a few MB)
+ *                          N <= 2^28; allocates 2 * F bytes (plus a few MB)
  *                          of stream-ordered scratch.
  * Errors: as skx_count; SKX_EINVAL for an unknown method; SKX_ENOTSUP when
- * SKX_COUNT_PARTITIONED is asked for with N > 2^26.
+ * SKX_COUNT_PARTITIONED is asked for with N > 2^28.
  */
 typedef enum {
     SKX_COUNT_AUTO = 0,

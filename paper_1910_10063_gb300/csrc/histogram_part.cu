@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kBktLog = 15;
 constexpr uint32_t kBkt = 1u << kBktLog;   // ids per bucket
-constexpr int kMaxBuckets = 2048;          // so N <= 2^26
+constexpr int kMaxBuckets = 8192;          // so N <= 2^28
 constexpr int kPBlock = 512;               // threads of phases A and C
 constexpr int kTileVec = 2048;             // 16-byte vectors per phase-C tile
 constexpr int kTileKeys = kTileVec * 4;    // 8192 keys

@@ -68,7 +68,7 @@ def test_argument_errors_without_gpu():
     assert L.skx_count_ex(P(16), 10, 5, P(16), 7, None) == skx.SKX_EINVAL
     assert L.skx_count_ex(P(16), 10, 5, P(16), -1, None) == skx.SKX_EINVAL
     assert L.skx_count_ex(P(16), 1 << 32, 5, P(16), skx.SKX_COUNT_AUTO, None) == skx.SKX_EINVAL
-    assert L.skx_count_ex(P(16), 10, (1 << 26) + 1, P(16), skx.SKX_COUNT_PARTITIONED, None) == skx.SKX_ENOTSUP
+    assert L.skx_count_ex(P(16), 10, (1 << 28) + 1, P(16), skx.SKX_COUNT_PARTITIONED, None) == skx.SKX_ENOTSUP
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

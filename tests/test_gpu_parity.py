@@ -170,7 +170,7 @@ def test_count_method_errors():
         skx.skx_count_ex(fk, 10, 7)
     assert e.value.status == skx.SKX_EINVAL
     with pytest.raises(skx.SkxError) as e:
-        skx.skx_count_ex(fk, (1 << 26) + 1, skx.SKX_COUNT_PARTITIONED,
+        skx.skx_count_ex(fk, (1 << 28) + 1, skx.SKX_COUNT_PARTITIONED,
                          counts=torch.empty(1, dtype=torch.int32, device=DEV))
     assert e.value.status == skx.SKX_ENOTSUP
 
