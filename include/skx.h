@@ -48,7 +48,7 @@ typedef enum skx_status {
     SKX_ECUDA = 5,       /* a CUDA runtime call failed (see skx_last_cuda_error) */
     SKX_ETIMEOUT = 6,    /* a bounded device-side wait expired */
     SKX_EBUSY = 7,       /* no free slot / resource (serving admission) */
-    SKX_ENOTSUP = 8      /* valid request this build does not support */
+    SKX_ENOTSUP = 8      /* valid request the library does not support */
 } skx_status;
 
 /* Human-readable name of a status code (static string, never NULL). */
