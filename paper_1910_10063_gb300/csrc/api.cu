@@ -56,6 +56,18 @@ void query_device(int d) {
 
 bool valid_stream_ptrs(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
 
+cudaStream_t g_copy_stream[kMaxDevices] = {};
+
+// A non-blocking stream per device for host-to-device copies that overlap the
+// kernels of the host-buffer path (created on first use, kept for the process).
+cudaStream_t copy_stream() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_copy_stream[d] && cudaStreamCreateWithFlags(&g_copy_stream[d], cudaStreamNonBlocking) != cudaSuccess)
+        g_copy_stream[d] = nullptr;
+    return g_copy_stream[d];
+}
+
 }  // namespace
 
 void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
@@ -428,28 +440,91 @@ skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_by
     // clear any stale error bits so this call reports only its own
     skx_status pre = skx_stream_status(stream);
     if (pre == SKX_ECUDA || pre == SKX_ENOMEM) return pre;
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    cudaStream_t cs = copy_stream();
+    if (!cs) return SKX_ECUDA;
 
+    // The host link, not HBM, bounds this path, so copies run on their own
+    // stream in the order the kernels need them -- fk, then the dimension
+    // rows, then the measure column in chunks -- and each kernel waits only
+    // for its inputs: the build and the remap overlap the copy of the rows,
+    // the reorder and the probe of each measure chunk overlap the copy of the
+    // next chunk.
+    constexpr int kChunks = 8;
+    const bool with_m = F > 0 && q->agg != SKX_AGG_COUNT;
+    const int nm = with_m ? kChunks : 0;
     char *d_rows = nullptr, *d_rows2 = nullptr;
     int32_t *d_fk = nullptr, *d_m = nullptr;
     int64_t *d_out = nullptr;
     skx_index *idx = nullptr;
+    cudaEvent_t ev_alloc = nullptr, ev_fk = nullptr, ev_rows = nullptr, ev_done = nullptr, ev_m[kChunks] = {};
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows), rows_b, st);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows2), rows_b, st);
     if (e == cudaSuccess && F > 0) e = cudaMallocAsync(reinterpret_cast<void **>(&d_fk), fk_b, st);
-    if (e == cudaSuccess && F > 0 && q->agg != SKX_AGG_COUNT) e = cudaMallocAsync(reinterpret_cast<void **>(&d_m), fk_b, st);
+    if (e == cudaSuccess && with_m) e = cudaMallocAsync(reinterpret_cast<void **>(&d_m), fk_b, st);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_out), size_t(nout) * 8, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rows, h_rows, rows_b, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && d_fk) e = cudaMemcpyAsync(d_fk, h_fk, fk_b, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && d_m) e = cudaMemcpyAsync(d_m, h_measure, fk_b, cudaMemcpyHostToDevice, st);
+    for (cudaEvent_t *ev : {&ev_alloc, &ev_fk, &ev_rows, &ev_done})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (int k = 0; k < nm && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev_m[k], cudaEventDisableTiming);
+    // chunk k of the measure column: rows [cut(k), cut(k + 1)), cuts on 16-byte boundaries
+    auto cut = [&](int k) { return k >= nm ? F : ((F * k / nm) & ~int64_t(3)); };
+    bool copies = false;
+    if (e == cudaSuccess) e = cudaEventRecord(ev_alloc, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_alloc, 0);
+    if (e == cudaSuccess) {
+        copies = true;
+        if (d_fk) e = cudaMemcpyAsync(d_fk, h_fk, fk_b, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_fk, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_rows, h_rows, rows_b, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_rows, cs);
+        for (int k = 0; k < nm && e == cudaSuccess; ++k) {
+            const int64_t a0 = cut(k), a1 = cut(k + 1);
+            if (a1 > a0)
+                e = cudaMemcpyAsync(d_m + a0, h_measure + a0, size_t(a1 - a0) * 4, cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_m[k], cs);
+        }
+        const cudaError_t e2 = cudaEventRecord(ev_done, cs);
+        if (e == cudaSuccess) e = e2;
+    }
     if (e != cudaSuccess) s = cuda_status(e);
+    if (s == SKX_OK) s = cudaStreamWaitEvent(st, ev_fk, 0) == cudaSuccess ? SKX_OK : SKX_ECUDA;
     if (s == SKX_OK) s = skx_build_index(d_fk, F, N, stream, &idx);
     if (s == SKX_OK) s = skx_remap(idx, d_fk, d_fk, F, stream);
+    if (s == SKX_OK) s = cudaStreamWaitEvent(st, ev_rows, 0) == cudaSuccess ? SKX_OK : SKX_ECUDA;
     if (s == SKX_OK) s = skx_reorder(idx, d_rows, d_rows2, N, row_bytes, stream);
-    if (s == SKX_OK) s = skx_probe_aggregate(d_rows2, N, row_bytes, d_fk, d_m, F, q, d_out, nullptr, stream);
+    if (s == SKX_OK) {
+        ProbeArgs a{};
+        a.rows = d_rows2;
+        a.N = N;
+        a.row_bytes = row_bytes;
+        a.q = *q;
+        a.out = d_out;
+        a.err = err;
+        skx_tuning t{};
+        cached_probe_tuning(N, row_bytes, *q, F, 1, &t);
+        const int parts = with_m ? nm : 1;
+        for (int k = 0; k < parts && s == SKX_OK; ++k) {
+            const int64_t a0 = with_m ? cut(k) : 0, a1 = with_m ? cut(k + 1) : F;
+            if (with_m && cudaStreamWaitEvent(st, ev_m[k], 0) != cudaSuccess) s = SKX_ECUDA;
+            a.fk = d_fk ? d_fk + a0 : nullptr;
+            a.measure = d_m ? d_m + a0 : nullptr;
+            a.F = a1 - a0;
+            a.accumulate = k > 0;
+            skx_tuning tk = t;
+            resolve_probe_tuning(a, tk);
+            if (s == SKX_OK) {
+                e = launch_probe(a, tk, st);
+                if (e != cudaSuccess) s = cuda_status(e);
+            }
+        }
+    }
     if (s == SKX_OK) {
         e = cudaMemcpyAsync(h_out, d_out, size_t(nout) * 8, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) s = cuda_status(e);
     }
+    // the buffers are freed in the compute stream's order: it first waits for every copy
+    if (copies) cudaStreamWaitEvent(st, ev_done, 0);
     skx_index_destroy(idx);
     if (d_rows) cudaFreeAsync(d_rows, st);
     if (d_rows2) cudaFreeAsync(d_rows2, st);
@@ -457,6 +532,10 @@ skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_by
     if (d_m) cudaFreeAsync(d_m, st);
     if (d_out) cudaFreeAsync(d_out, st);
     skx_status fin = skx_stream_status(stream);
+    for (cudaEvent_t ev : {ev_alloc, ev_fk, ev_rows, ev_done})
+        if (ev) cudaEventDestroy(ev);
+    for (int k = 0; k < nm; ++k)
+        if (ev_m[k]) cudaEventDestroy(ev_m[k]);
     return s != SKX_OK ? s : fin;
 }
 

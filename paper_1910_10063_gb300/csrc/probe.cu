@@ -278,7 +278,7 @@ cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t s
     p.out = reinterpret_cast<unsigned long long *>(a.out);
     p.err = a.err;
     const int nout = a.q.agg == SKX_AGG_GROUPBY_SUM ? a.q.num_groups : 1;
-    cudaError_t e = cudaMemsetAsync(a.out, 0, size_t(nout) * 8, st);
+    cudaError_t e = a.accumulate ? cudaSuccess : cudaMemsetAsync(a.out, 0, size_t(nout) * 8, st);
     if (e != cudaSuccess || a.F <= 0) return e;
 
     // vector path needs fk and measure at the same offset mod 16 bytes

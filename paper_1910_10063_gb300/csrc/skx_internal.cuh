@@ -192,6 +192,7 @@ struct ProbeArgs {
     skx_query q;
     int64_t *out;
     unsigned *err;
+    bool accumulate;  // add into out instead of overwriting it (probing a column in chunks)
 };
 // Resolves defaults in `t` (in place) for these arguments.
 void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t);

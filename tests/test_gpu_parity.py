@@ -618,6 +618,23 @@ def test_join_aggregate_host_api():
         assert np.array_equal(got, _oracle(dim, fk, m, d))
 
 
+@pytest.mark.parametrize("f", [0, 1, 3, 7, 33, 4099, 1_000_003])
+def test_join_aggregate_host_chunked_copies(f):
+    """The host path copies the measure column in chunks cut on 16-byte
+    boundaries and probes each as it lands: ragged and tiny columns, pinned
+    host tensors, and a second call reusing the copy stream."""
+    w = synth.Workload(5_000, f, 1.2, seed=19, width=16)
+    fk, m, dim = w.fk(), w.measure(), w.dim()
+    hfk = torch.from_numpy(fk).pin_memory()
+    hm = torch.from_numpy(m).pin_memory()
+    hdim = torch.from_numpy(dim).pin_memory()
+    for qname in ("groupby", "count"):
+        d = QUERIES[qname]
+        want = _oracle(dim, fk, m, d)
+        for _ in range(2):
+            assert np.array_equal(skx.skx_join_aggregate_host(hdim, hfk, hm, _q(d)), want)
+
+
 def test_autotune_choice_is_exact_and_cached(probe_data):
     d = QUERIES["groupby"]
     want = _oracle(probe_data["dim"], probe_data["fk"], probe_data["m"], d)
