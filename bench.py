@@ -52,6 +52,11 @@ def parse_args():
     p.add_argument("--sweep", default="0.0,0.5,1.0,1.5", help="Zipf exponents of the plain-vs-remapped probe sweep")
     p.add_argument("--sweep-steps", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--count-method", choices=["auto", "single", "partitioned"], default="auto",
+                   help="count algorithm of the timed step (skx_count_ex); the library's automatic choice by default")
+    p.add_argument("--tuning", default="",
+                   help="probe tuning of the timed step as field=value,... (e.g. block_threads=256,ctas_per_sm=8,"
+                        "unroll=1,hot_keys=-1,lane_keys=-1) instead of the autotuner's choice; for profiling")
     p.add_argument("--batch-queries", type=int, default=512, help="queries of the batched workload (0 = skip)")
     p.add_argument("--serve-n", type=int, default=50_000_000, help="rows of the served dimension table (0 = skip)")
     p.add_argument("--serve-pool", type=int, default=256, help="distinct requests in the serving pool")
@@ -72,7 +77,9 @@ def config_of(a, world):
             "num_groups": 1000, "filter": "attr1 < 50", "accumulate": "int64", "seed": a.seed,
             "l2": "flushed before every timed step (512 MB write, outside the timed events); "
                   "fact inputs (4 GB/step) are also far larger than L2",
-            "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"}
+            "parallelism": "single GPU" if world == 1 else f"{world} independent replicas",
+            "count_method": getattr(a, "count_method", "auto"),
+            "probe_tuning": "autotuned" if not getattr(a, "tuning", "") else a.tuning}
 
 
 def hbm_peak():
@@ -96,9 +103,10 @@ def source_sha(path):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged.
-    A key "a+b+c" sums the kernels of a stage that runs several."""
+def ncu_traffic(kernel_key, a=None):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged and
+    the capture was taken on this workload.  A key "a+b+c" sums the kernels of a stage that runs
+    several."""
     try:
         with open(TRAFFIC_PATH) as fh:
             table = json.load(fh)
@@ -107,17 +115,24 @@ def ncu_traffic(kernel_key):
             rec = table[k]
             if source_sha(os.path.join(ROOT, rec["source"])) != rec["source_sha"]:
                 return None
+            if a is not None and rec.get("shape") != [a.n, a.f, a.s, a.width * 4]:
+                return None
             total += rec["bytes_per_launch"]
         return total
     except Exception:
         return None
 
 
-def count_kernels(fk, n, f):
+COUNT_METHODS = {"auto": 0, "single": 1, "partitioned": 2}
+
+
+def count_kernels(fk, n, f, method="auto"):
     """Kernels the library's automatic count runs on this column: it samples 8192 keys at stride
     f // 8192 on the device and takes the partitioned count (2^24 <= n <= 2^28, f >= 2^28) unless
     60 % or more of the sampled keys repeat in the sample.  The same rule, evaluated here, only
     labels the stage in the report."""
+    if method != "auto":
+        return "k_histogram" if method == "single" else "k_part_count+k_part_scatter+k_part_hist"
     if not (2 ** 24 <= n <= 2 ** 28 and f >= 2 ** 28):
         return "k_histogram"
     sample = fk[:: f // 8192][:8192].cpu().numpy()
@@ -218,12 +233,18 @@ def run_ours(a, rank, world, local_rank):
     idx0 = skx.skx_build_index(w.fk, a.n)
     skx.skx_remap(idx0, w.fk, fk2)
     skx.skx_reorder(idx0, w.dim, dim2)
-    tuning, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True)
+    if a.tuning:
+        tuning = skx.Tuning()
+        for kv in a.tuning.split(","):
+            k, v = kv.split("=")
+            setattr(tuning, k.strip(), int(v))
+    else:
+        tuning, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True)
     idx0.close()
 
     def step(ev):
         ev[0].record(stream)
-        skx.skx_count(w.fk, a.n, counts)
+        skx.skx_count_ex(w.fk, a.n, COUNT_METHODS[a.count_method], counts=counts)
         ev[1].record(stream)
         idx = skx.skx_build_index_from_counts(counts, a.f)
         ev[2].record(stream)
@@ -277,7 +298,7 @@ def run_ours(a, rank, world, local_rank):
 
     def step_q8(ev):
         ev[0].record(stream)
-        skx.skx_count(w.fk, a.n, counts)
+        skx.skx_count_ex(w.fk, a.n, COUNT_METHODS[a.count_method], counts=counts)
         ev[1].record(stream)
         idx = skx.skx_build_index_from_counts(counts, a.f)
         ev[2].record(stream)
@@ -319,18 +340,18 @@ def run_ours(a, rank, world, local_rank):
     row_b = a.width * 4
     alg = {"count": 4 * a.f + 4 * a.n, "sort": 12 * a.n, "remap": 8 * a.f + 4 * a.n,
            "reorder": 2 * row_b * a.n + 4 * a.n, "probe": 8 * a.f + 16 * D}
-    kernel_of = {"count": count_kernels(w.fk, a.n, a.f), "sort": "k_radix_*", "remap": "k_remap", "reorder": "k_reorder",
+    kernel_of = {"count": count_kernels(w.fk, a.n, a.f, a.count_method), "sort": "k_radix_*", "remap": "k_remap", "reorder": "k_reorder",
                  "probe": "k_probe"}
     stage_avg = {s: statistics.mean(v) for s, v in stage_ms.items()}
     stage_rep = {s: {"ms": round(stage_avg[s], 4), "alg_bytes": int(alg[s]),
                      "gbs": round(alg[s] / (stage_avg[s] * 1e-3) / 1e9, 1),
                      "frac": round(alg[s] / (stage_avg[s] * 1e-3) / 1e9 / peak, 4),
-                     "kernel": kernel_of[s], "dram_bytes": ncu_traffic(kernel_of[s])} for s in stages}
+                     "kernel": kernel_of[s], "dram_bytes": ncu_traffic(kernel_of[s], a)} for s in stages}
     dom = max(stages, key=lambda s: stage_avg[s])
     achieved = alg[dom] / (stage_avg[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kernel_of[dom], "stage": dom, "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} hbm_gbs",
-                "alg_bytes_per_launch": int(alg[dom]), "traffic": ncu_traffic(kernel_of[dom]),
+                "alg_bytes_per_launch": int(alg[dom]), "traffic": ncu_traffic(kernel_of[dom], a),
                 "algorithmic_bytes": {"count": "4F + 4N", "sort": "12N (read counts, write perm and rank)",
                                       "remap": "8F + 4N", "reorder": "2*row_bytes*N + 4N",
                                       "probe": f"8F + 16*D, D = expected distinct keys = {D:.4g}"}[dom]}
