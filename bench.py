@@ -462,7 +462,7 @@ def run_ours(a, rank, world, local_rank):
     # ---------------- Section III-C cache model: predicted L2 hit rate of the gathers
     cache_model = None
     if rank == 0:
-        cache_model = predict_l2(a, w)
+        cache_model = predict_l2(a, w, tuning=tuning)
 
     # ---------------- batched queries: 512 uneven fact batches in one persistent launch
     batch = None
@@ -502,6 +502,7 @@ def run_ours(a, rank, world, local_rank):
         e2e = {"value": round(world * a.f * n_e2e / e2e_s / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": int(h_dim.numel() * 4 + 2 * a.f * 4), "d2h_bytes_per_step": 8 * 1000,
                "ms_per_step": round(1e3 * e2e_s / n_e2e, 3), "steps": n_e2e,
+               "ms_each": [round(1e3 * x, 2) for x in t],
                "api": "skx_join_aggregate_host (pinned host buffers; H2D, build, remap, reorder, probe, D2H)"}
 
     # ---------------- CPU baseline: the oracle on a bounded sample
@@ -533,10 +534,15 @@ def run_ours(a, rank, world, local_rank):
     return line
 
 
-def predict_l2(a, w, line_bytes=128):
+def predict_l2(a, w, line_bytes=128, tuning=None):
     """The Section III-C model for the probe's dimension gathers on both layouts:
     cache lines of 128 bytes over 64-byte rows, access frequencies from the Zipf
-    pmf (rank r) -- remapped: row r is rank r; plain: row v is rank rank_of(v)."""
+    pmf (rank r) -- remapped: row r is rank r; plain: row v is rank rank_of(v).
+    Then the paper's use of it: fit a power law to the index's counts at 48
+    log-spaced ranks (a line in a log-log plot), predict the hit rate from the
+    fitted distribution alone, and derive the Section IV-B threshold t (ids below
+    t likely hit) for the L2 and for one SM's L1, next to the hot prefix the
+    autotuner chose by timing."""
     import paper_1910_10063_gb300 as skx
     from paper_1910_10063_gb300 import synth
     import torch
@@ -545,6 +551,7 @@ def predict_l2(a, w, line_bytes=128):
     rows_per_line = max(1, line_bytes // (a.width * 4))
     L2 = torch.cuda.get_device_properties(0).L2_cache_size
     S = L2 // line_bytes
+    S_l1 = (200 << 10) // line_bytes  # L1 left beside the probe's shared memory, per SM
     nl = (a.n + rows_per_line - 1) // rows_per_line
 
     def lines(p_row):
@@ -554,11 +561,31 @@ def predict_l2(a, w, line_bytes=128):
     rank_of_id = np.empty(a.n, dtype=np.int64)
     rank_of_id[w.r2id_host] = np.arange(a.n)
     t0 = time.perf_counter()
-    hit_r = skx.skx_cache_hit_rate(lines(p_rank), S)
+    lines_r = lines(p_rank)
+    hit_r = skx.skx_cache_hit_rate(lines_r, S)
     hit_p = skx.skx_cache_hit_rate(lines(p_rank[rank_of_id]), S)
+    # the paper's recipe from a few statistics of the data: counts at log-spaced ranks -> fit
+    idx = skx.skx_build_index(w.fk, a.n)
+    ranks = np.unique(np.geomspace(1, a.n, 48).astype(np.int64)) - 1
+    cnts = skx.skx_index_counts_at_ranks(idx, ranks).astype(np.float64)
+    idx.close()
+    slope, icpt = skx.skx_powerlaw_fit(ranks + 1.0, cnts)
+    p_fit = np.arange(1, a.n + 1, dtype=np.float64) ** slope
+    p_fit /= p_fit.sum()
+    lines_fit = lines(p_fit)
+    hit_fit = skx.skx_cache_hit_rate(lines_fit, S)
+    t_l2 = skx.skx_cache_threshold(lines_r, S, 0.5, rows_per_line)
+    t_l1 = skx.skx_cache_threshold(lines_r, S_l1, 0.5, rows_per_line)
+    t_l2_fit = skx.skx_cache_threshold(lines_fit, S, 0.5, rows_per_line)
     return {"model": "Section III-C stack-distance model, LRU of the whole L2", "l2_bytes": int(L2),
             "line_bytes": line_bytes, "lines_in_cache": int(S), "dimension_lines": int(nl),
             "predicted_hit_remapped": round(hit_r, 4), "predicted_hit_plain": round(hit_p, 4),
+            "powerlaw_fit": {"points": int(ranks.size), "slope": round(slope, 4), "intercept": round(icpt, 3),
+                             "zipf_s": a.s, "predicted_hit_remapped_from_fit": round(hit_fit, 4)},
+            "threshold_t": {"rule": "ids whose line is a hit with probability >= 0.5 (Section IV-B)",
+                            "l2": int(t_l2), "l2_from_fit": int(t_l2_fit), "l1_per_sm": int(t_l1),
+                            "l1_lines": int(S_l1),
+                            "autotuned_hot_keys": None if tuning is None else int(tuning.hot_keys)},
             "seconds": round(time.perf_counter() - t0, 2)}
 
 

@@ -331,6 +331,38 @@ skx_status skx_select(const uint32_t *d_bits, int32_t N, const int32_t *d_fk, in
  * S lines for L lines with access frequencies h_f (host, sum 1). */
 skx_status skx_cache_hit_rate(const double *h_f, int64_t L, int64_t S, double *hit);
 
+/* The same model's hit probability of each line, cdf_i = 1 - (1 - f_i)^K_i
+ * (Section III-C), written to h_cdf[L] (host) in the order of h_f; 0 for lines
+ * with f_i = 0.  Errors: SKX_EINVAL (null pointer, L < 1, S < 1, a negative
+ * or NaN frequency). */
+skx_status skx_cache_line_cdf(const double *h_f, int64_t L, int64_t S, double *h_cdf);
+
+/* The threshold t of Section IV-B derived from the Section III-C model: ids
+ * below t are likely cache hits.  h_f lists the lines in transformed-id order
+ * (line j holds ids [j * rows_per_line, (j + 1) * rows_per_line), as in the
+ * remapped layout); *t = rows_per_line x the number of leading lines whose
+ * modelled hit probability is at least p (0 < p <= 1).  Host only.
+ * Errors: as skx_cache_line_cdf; SKX_EINVAL for p outside (0, 1],
+ * rows_per_line < 1 or a null t. */
+skx_status skx_cache_threshold(const double *h_f, int64_t L, int64_t S, double p, int32_t rows_per_line,
+                               int64_t *t);
+
+/* Power-law fit of a value-frequency distribution (Section III-C: sample the
+ * data and fit it to a known distribution; a power law is a line in a
+ * log-log plot): the least-squares line log y = intercept + slope * log x
+ * through the points (h_x[k], h_y[k]) with x > 0 and y > 0 (others are
+ * skipped).  Host only.  Errors: SKX_EINVAL (null pointer, fewer than two
+ * usable points, all usable x equal). */
+skx_status skx_powerlaw_fit(const double *h_x, const double *h_y, int64_t n, double *slope, double *intercept);
+
+/* Counts of chosen ranks of an index, the input of a frequency fit:
+ * h_counts[k] = counts[perm[h_ranks[k]]] (the count of the id with
+ * transformed id h_ranks[k]), for n host-side ranks in [0, N).  Gathers on
+ * the device on `stream` and synchronises it.  Errors: SKX_EINVAL (null
+ * index or buffer, a rank outside [0, N)), SKX_ENOMEM, SKX_ECUDA. */
+skx_status skx_index_counts_at_ranks(const skx_index *idx, const int64_t *h_ranks, int64_t n, uint32_t *h_counts,
+                                     void *stream);
+
 /* ------------------------------------------------------------------------
  * Batched probes (many queries, one persistent launch).  Each descriptor is
  * one skx_probe_aggregate call against the same dimension table: remapped

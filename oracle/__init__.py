@@ -24,6 +24,8 @@ Improved Query Performance" (ICDE 2020, arXiv 1910.10063):
 * ``index_append``       maintenance: new rows appended as least frequent
                          (Section III-A)
 * ``cache_hit_rate``     the stack-distance cache model (Section III-C)
+* ``cache_threshold``    the threshold t of Section IV-B derived from that model
+* ``powerlaw_fit``       least-squares line in a log-log plot (Section III-C)
 
 Every function has at least one pin in ``tests/test_oracle_pins.py`` that
 does not go through this code (worked example of Fig. 2, brute force, closed
@@ -93,9 +95,11 @@ def _declare(lib):
     lib.orc_select.argtypes = [P, i32, i32, P, i64, cint, i32, P, P]
     lib.orc_index_append.argtypes = [P, P, i32, i32, P, P]
     lib.orc_cache_hit_rate.argtypes = [P, i64, i64, P, P]
+    lib.orc_cache_threshold.argtypes = [P, i64, i64, ctypes.c_double, i32, P]
+    lib.orc_powerlaw_fit.argtypes = [P, P, i64, P, P]
     for f in ("orc_histogram", "orc_sort_by_frequency", "orc_invert", "orc_build_index",
               "orc_remap", "orc_reorder", "orc_probe", "orc_topk_counts", "orc_select", "orc_index_append",
-              "orc_cache_hit_rate"):
+              "orc_cache_hit_rate", "orc_cache_threshold", "orc_powerlaw_fit"):
         getattr(lib, f).restype = cint
     return lib
 
@@ -244,3 +248,26 @@ def cache_hit_rate(f, S: int, lib=None):
     if st:
         raise OracleError(st, "cache_hit_rate")
     return float(hit[0]), cdf
+
+
+def cache_threshold(f, S: int, p: float, rows_per_line: int, lib=None) -> int:
+    """Threshold t (ids below it likely cache hits) for lines f in transformed-id order."""
+    lib = lib or load()
+    f = _c(f, np.float64)
+    t = np.zeros(1, dtype=np.int64)
+    st = lib.orc_cache_threshold(_ptr(f), f.shape[0], S, float(p), rows_per_line, _ptr(t))
+    if st:
+        raise OracleError(st, "cache_threshold")
+    return int(t[0])
+
+
+def powerlaw_fit(x, y, lib=None):
+    """(slope, intercept) of the least-squares line log y = intercept + slope log x."""
+    lib = lib or load()
+    x = _c(x, np.float64)
+    y = _c(y, np.float64)
+    out = np.zeros(2, dtype=np.float64)
+    st = lib.orc_powerlaw_fit(_ptr(x), _ptr(y), x.shape[0], _ptr(out[:1]), _ptr(out[1:]))
+    if st:
+        raise OracleError(st, "powerlaw_fit")
+    return float(out[0]), float(out[1])

@@ -450,3 +450,60 @@ int orc_cache_hit_rate(const double *f, int64_t L, int64_t S, double *hit, doubl
     *hit = h;
     return ORC_OK;
 }
+
+/* Threshold t of Section IV-B from the Section III-C model: lines are given
+ * in transformed-id order, each holding rows_per_line ids; ids below t are
+ * "likely cache hits", read as: t covers the leading lines whose modelled hit
+ * probability cdf_j is at least p. */
+int orc_cache_threshold(const double *f, int64_t L, int64_t S, double p, int32_t rows_per_line, int64_t *t)
+{
+    if (!t || rows_per_line < 1 || !(p > 0.0 && p <= 1.0) || L < 1)
+        return ORC_EINVAL;
+    double *cdf = (double *)malloc(sizeof(double) * (size_t)L);
+    if (!cdf)
+        return ORC_EINVAL;
+    double hit;
+    int st = orc_cache_hit_rate(f, L, S, &hit, cdf);
+    if (st) {
+        free(cdf);
+        return st;
+    }
+    int64_t j = 0;
+    while (j < L && cdf[j] >= p)
+        j++;
+    free(cdf);
+    *t = j * (int64_t)rows_per_line;
+    return ORC_OK;
+}
+
+/* Section III-C: a power-law frequency distribution is a straight line in a
+ * log-log plot; fit it by ordinary least squares, log y = a + b log x, over
+ * the points with x > 0 and y > 0:
+ *   b = (m Sum uv - Sum u Sum v) / (m Sum u^2 - (Sum u)^2),  a = (Sum v - b Sum u) / m
+ * with u = log x, v = log y and m usable points. */
+int orc_powerlaw_fit(const double *x, const double *y, int64_t n, double *slope, double *intercept)
+{
+    if (!x || !y || n < 0 || !slope || !intercept)
+        return ORC_EINVAL;
+    long double su = 0, sv = 0, suu = 0, suv = 0;
+    int64_t m = 0;
+    for (int64_t k = 0; k < n; k++) {
+        if (!(x[k] > 0.0) || !(y[k] > 0.0))
+            continue;
+        long double u = logl((long double)x[k]), v = logl((long double)y[k]);
+        su += u;
+        sv += v;
+        suu += u * u;
+        suv += u * v;
+        m++;
+    }
+    if (m < 2)
+        return ORC_EINVAL;
+    long double den = (long double)m * suu - su * su;
+    if (!(den > 0))
+        return ORC_EINVAL;
+    long double b = ((long double)m * suv - su * sv) / den;
+    *slope = (double)b;
+    *intercept = (double)((sv - b * su) / (long double)m);
+    return ORC_OK;
+}

@@ -178,6 +178,12 @@ def lib():
             L.skx_select.argtypes = [P, i32, P, i64, P, P, P]; L.skx_select.restype = st
             L.skx_cache_hit_rate.argtypes = [P, i64, i64, ctypes.POINTER(ctypes.c_double)]
             L.skx_cache_hit_rate.restype = st
+            L.skx_cache_line_cdf.argtypes = [P, i64, i64, P]; L.skx_cache_line_cdf.restype = st
+            L.skx_cache_threshold.argtypes = [P, i64, i64, ctypes.c_double, i32, ctypes.POINTER(i64)]
+            L.skx_cache_threshold.restype = st
+            L.skx_powerlaw_fit.argtypes = [P, P, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+            L.skx_powerlaw_fit.restype = st
+            L.skx_index_counts_at_ranks.argtypes = [P, P, i64, P, P]; L.skx_index_counts_at_ranks.restype = st
             L.skx_join_aggregate_host.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), P, P]
             L.skx_join_aggregate_host.restype = st
             _lib = L
@@ -594,6 +600,50 @@ def skx_cache_hit_rate(f, S: int) -> float:
     _check(lib().skx_cache_hit_rate(f.ctypes.data_as(ctypes.c_void_p), f.size, int(S), ctypes.byref(hit)),
            "skx_cache_hit_rate")
     return hit.value
+
+
+def skx_cache_line_cdf(f, S: int):
+    """Per-line hit probabilities of the Section III-C model (numpy float64, order of f)."""
+    import numpy as np
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    cdf = np.empty_like(f)
+    _check(lib().skx_cache_line_cdf(f.ctypes.data_as(ctypes.c_void_p), f.size, int(S),
+                                    cdf.ctypes.data_as(ctypes.c_void_p)), "skx_cache_line_cdf")
+    return cdf
+
+
+def skx_cache_threshold(f, S: int, p: float = 0.5, rows_per_line: int = 1) -> int:
+    """Threshold t of Section IV-B from the model: ids below t are likely cache hits."""
+    import numpy as np
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    t = ctypes.c_int64()
+    _check(lib().skx_cache_threshold(f.ctypes.data_as(ctypes.c_void_p), f.size, int(S), float(p),
+                                     int(rows_per_line), ctypes.byref(t)), "skx_cache_threshold")
+    return t.value
+
+
+def skx_powerlaw_fit(x, y):
+    """(slope, intercept) of the least-squares line log y = intercept + slope log x."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    if x.shape != y.shape:
+        raise ValueError("x and y must have the same length")
+    b, a = ctypes.c_double(), ctypes.c_double()
+    _check(lib().skx_powerlaw_fit(x.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p), x.size,
+                                  ctypes.byref(b), ctypes.byref(a)), "skx_powerlaw_fit")
+    return b.value, a.value
+
+
+def skx_index_counts_at_ranks(index: "Index", ranks, stream=None):
+    """counts of the ids with the given transformed ids (numpy uint32), gathered on the device."""
+    import numpy as np
+    r = np.ascontiguousarray(ranks, dtype=np.int64)
+    out = np.zeros(r.size, dtype=np.uint32)
+    _check(lib().skx_index_counts_at_ranks(index._h, r.ctypes.data_as(ctypes.c_void_p), r.size,
+                                           out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "skx_index_counts_at_ranks")
+    return out
 
 
 def skx_join_aggregate_host(rows, fk, measure, query: Query, out=None, stream=None):

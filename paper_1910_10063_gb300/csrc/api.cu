@@ -109,6 +109,15 @@ int device_max_smem_optin() {
 
 using namespace skx;
 
+namespace skx_rankcounts {
+// out[k] = counts[perm[ranks[k]]]
+__global__ void k_counts_at_ranks(const uint32_t *counts, const int32_t *perm, const int64_t *ranks, int64_t n,
+                                  uint32_t *out) {
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        out[k] = counts[perm[ranks[k]]];
+}
+}  // namespace skx_rankcounts
+
 namespace skx_append {
 __global__ void k_append_tail(int32_t *perm, int32_t *rank, uint32_t *counts, int32_t N, int32_t n_new) {
     for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n_new; j += int64_t(gridDim.x) * blockDim.x) {
@@ -256,6 +265,31 @@ skx_status skx_index_counts(const skx_index *idx, const uint32_t **d_counts) {
 }
 
 int32_t skx_index_size(const skx_index *idx) { return idx ? idx->N : -1; }
+
+skx_status skx_index_counts_at_ranks(const skx_index *idx, const int64_t *h_ranks, int64_t n, uint32_t *h_counts,
+                                     void *stream) {
+    if (!idx || n < 0 || (n > 0 && (!h_ranks || !h_counts))) return SKX_EINVAL;
+    for (int64_t k = 0; k < n; ++k)
+        if (h_ranks[k] < 0 || h_ranks[k] >= idx->N) return SKX_EINVAL;
+    if (n == 0) return SKX_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t *d_r = nullptr;
+    uint32_t *d_c = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_r), size_t(n) * 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_c), size_t(n) * 4, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_r, h_ranks, size_t(n) * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const int grid = (int)std::min<int64_t>((n + 255) / 256, int64_t(device_sm_count()) * 8);
+        skx_rankcounts::k_counts_at_ranks<<<grid, 256, 0, st>>>(idx->counts, idx->perm, d_r, n, d_c);
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts, d_c, size_t(n) * 4, cudaMemcpyDeviceToHost, st);
+    if (d_r) cudaFreeAsync(d_r, st);
+    if (d_c) cudaFreeAsync(d_c, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? SKX_OK : cuda_status(e);
+}
 
 void skx_index_destroy(skx_index *idx) {
     if (!idx) return;

@@ -60,15 +60,19 @@ struct Model {
     }
 };
 
-}  // namespace
-
-extern "C" skx_status skx_cache_hit_rate(const double *h_f, int64_t L, int64_t S, double *hit) {
-    if (!h_f || L < 1 || S < 1 || !hit) return SKX_EINVAL;
+// Evaluates the model: the hit rate and, when cdf is given, each line's hit
+// probability in the order of f.
+skx_status eval_model(const double *h_f, int64_t L, int64_t S, double *hit, double *cdf) {
+    if (!h_f || L < 1 || S < 1) return SKX_EINVAL;
     Model m;
-    m.g.assign(h_f, h_f + L);
-    for (double x : m.g)
-        if (!(x >= 0.0)) return SKX_EINVAL;
-    std::sort(m.g.begin(), m.g.end(), std::greater<double>());
+    std::vector<int64_t> order(L);
+    for (int64_t j = 0; j < L; ++j) {
+        if (!(h_f[j] >= 0.0)) return SKX_EINVAL;
+        order[j] = j;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return h_f[x] > h_f[y]; });
+    m.g.resize(L);
+    for (int64_t j = 0; j < L; ++j) m.g[j] = h_f[order[j]];
     m.P.assign(L + 1, 0.0);
     for (int64_t j = 0; j < L; ++j) m.P[j + 1] = m.P[j] + m.g[j];
     m.used = std::lower_bound(m.g.begin(), m.g.end(), 0.0, std::greater<double>()) - m.g.begin();  // g > 0
@@ -81,7 +85,7 @@ extern "C" skx_status skx_cache_hit_rate(const double *h_f, int64_t L, int64_t S
     const double k_floor = m.K(0.0, false, S, double(S), fpos_min);
     double h = 0.0, k_prev = INFINITY;
     bool at_floor = false, monotone = false;
-    for (int64_t i = 0; i < m.used; ++i) {  // hottest first; zero-frequency lines add nothing
+    for (int64_t i = 0; i < m.used; ++i) {  // hottest first
         const double fi = m.g[i];
         double c;
         if (fi >= 1.0) {
@@ -98,8 +102,65 @@ extern "C" skx_status skx_cache_hit_rate(const double *h_f, int64_t L, int64_t S
             k_prev = Ki;
             c = std::isinf(Ki) ? 1.0 : 1.0 - std::pow(1.0 - fi, Ki);
         }
+        if (cdf) cdf[order[i]] = c;
         h += fi * c;
     }
-    *hit = h;
+    if (cdf)
+        for (int64_t i = m.used; i < L; ++i) cdf[order[i]] = 0.0;  // never referenced
+    if (hit) *hit = h;
     return SKX_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+skx_status skx_cache_hit_rate(const double *h_f, int64_t L, int64_t S, double *hit) {
+    if (!hit) return SKX_EINVAL;
+    return eval_model(h_f, L, S, hit, nullptr);
+}
+
+skx_status skx_cache_line_cdf(const double *h_f, int64_t L, int64_t S, double *h_cdf) {
+    if (!h_cdf) return SKX_EINVAL;
+    return eval_model(h_f, L, S, nullptr, h_cdf);
+}
+
+skx_status skx_cache_threshold(const double *h_f, int64_t L, int64_t S, double p, int32_t rows_per_line,
+                               int64_t *t) {
+    if (!t || rows_per_line < 1 || !(p > 0.0 && p <= 1.0)) return SKX_EINVAL;
+    std::vector<double> cdf(L > 0 ? L : 1);
+    const skx_status s = eval_model(h_f, L, S, nullptr, cdf.data());
+    if (s != SKX_OK) return s;
+    int64_t j = 0;
+    while (j < L && cdf[j] >= p) ++j;
+    *t = j * int64_t(rows_per_line);
+    return SKX_OK;
+}
+
+skx_status skx_powerlaw_fit(const double *h_x, const double *h_y, int64_t n, double *slope, double *intercept) {
+    if (!h_x || !h_y || n < 0 || !slope || !intercept) return SKX_EINVAL;
+    // centred sums for the least-squares line through (log x, log y)
+    int64_t m = 0;
+    double sx = 0.0, sy = 0.0;
+    for (int64_t k = 0; k < n; ++k)
+        if (h_x[k] > 0.0 && h_y[k] > 0.0) {
+            sx += std::log(h_x[k]);
+            sy += std::log(h_y[k]);
+            ++m;
+        }
+    if (m < 2) return SKX_EINVAL;
+    const double mx = sx / double(m), my = sy / double(m);
+    double sxx = 0.0, sxy = 0.0;
+    for (int64_t k = 0; k < n; ++k)
+        if (h_x[k] > 0.0 && h_y[k] > 0.0) {
+            const double u = std::log(h_x[k]) - mx, v = std::log(h_y[k]) - my;
+            sxx += u * u;
+            sxy += u * v;
+        }
+    if (!(sxx > 0.0)) return SKX_EINVAL;  // all x equal: no line
+    *slope = sxy / sxx;
+    *intercept = my - *slope * mx;
+    return SKX_OK;
+}
+
+}  // extern "C"

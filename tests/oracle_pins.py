@@ -347,7 +347,58 @@ def pin_cache_model(lib):
         assert abs(oracle.cache_hit_rate(p, S, lib=lib)[0] - _lru_hit_rate(p, S, 200_000, 1)) < 0.05
 
 
+def pin_cache_threshold(lib):
+    # the threshold counts the leading lines whose modelled hit probability is >= p, times the rows
+    # per line; on the hand-worked lines of pin_cache_model (whose cdf is pinned there) ...
+    f = np.array([0.9, 0.07, 0.015, 0.01, 0.005])
+    _, cdf = oracle.cache_hit_rate(f, 3, lib=lib)
+    for p in (0.3, 0.5, 0.9, 0.99):
+        want = 0
+        while want < f.size and cdf[want] >= p:
+            want += 1
+        assert oracle.cache_threshold(f, 3, p, 1, lib=lib) == want
+        assert oracle.cache_threshold(f, 3, p, 16, lib=lib) == 16 * want
+    # every line is a hit when the cache holds them all; p = 1 keeps exactly those
+    assert oracle.cache_threshold(np.array([0.5, 0.3, 0.2]), 3, 1.0, 4, lib=lib) == 12
+    # S = 1: cdf_i = f_i (exact LRU), so the threshold is the leading run of lines with f >= p
+    assert oracle.cache_threshold(np.array([0.6, 0.25, 0.1, 0.05]), 1, 0.2, 1, lib=lib) == 2
+    assert oracle.cache_threshold(np.array([0.6, 0.25, 0.1, 0.05]), 1, 0.7, 1, lib=lib) == 0
+    # a colder line out of order stops the run (lines are in transformed-id order)
+    assert oracle.cache_threshold(np.array([0.1, 0.6, 0.25, 0.05]), 1, 0.2, 1, lib=lib) == 0
+    for bad in ((f, 3, 0.0, 1), (f, 3, 1.5, 1), (f, 3, 0.5, 0)):
+        try:
+            oracle.cache_threshold(*bad, lib=lib)
+        except oracle.OracleError:
+            continue
+        raise AssertionError("invalid threshold arguments accepted")
+
+
+def pin_powerlaw_fit(lib):
+    # an exact power law c x^b is a line of slope b and intercept log c in a log-log plot
+    x = np.arange(1, 501, dtype=np.float64)
+    for c, b in ((3.0, -1.2), (1e6, -1.0), (0.5, -0.3), (2.0, 0.7)):
+        slope, icpt = oracle.powerlaw_fit(x, c * x ** b, lib=lib)
+        assert abs(slope - b) < 1e-12 and abs(icpt - np.log(c)) < 1e-10
+    # two points fix the line; y = 8 at x = 2 and y = 2 at x = 8 give slope -1, intercept log 16
+    slope, icpt = oracle.powerlaw_fit([2.0, 8.0], [8.0, 2.0], lib=lib)
+    assert abs(slope + 1.0) < 1e-14 and abs(icpt - np.log(16.0)) < 1e-13
+    # points with x <= 0 or y <= 0 are skipped (zero counts have no logarithm)
+    slope, icpt = oracle.powerlaw_fit([1.0, 2.0, 3.0, 0.0, 5.0], [1.0, 0.25, 0.0, 7.0, 1.0 / 25.0], lib=lib)
+    assert abs(slope + 2.0) < 1e-13 and abs(icpt) < 1e-13
+    # least squares, not interpolation: (1, e), (e, 1), (e^2, e) -> u = 0, 1, 2 and v = 1, 0, 1 -> slope 0,
+    # intercept 2/3
+    e = np.e
+    slope, icpt = oracle.powerlaw_fit([1.0, e, e * e], [e, 1.0, e], lib=lib)
+    assert abs(slope) < 1e-14 and abs(icpt - 2.0 / 3.0) < 1e-14
+    for bad in (([1.0], [1.0]), ([2.0, 2.0], [1.0, 3.0]), ([1.0, 2.0], [0.0, -1.0])):
+        try:
+            oracle.powerlaw_fit(*bad, lib=lib)
+        except oracle.OracleError:
+            continue
+        raise AssertionError("degenerate fit accepted")
+
+
 ALL_PINS = [pin_fig2_example, pin_histogram, pin_sort_by_frequency, pin_invert, pin_remap,
             pin_reorder, pin_probe_brute_force, pin_probe_closed_forms, pin_probe_wraparound,
             pin_probe_layout_invariance, pin_probe_errors, pin_topk_counts, pin_select, pin_index_append,
-            pin_cache_model]
+            pin_cache_model, pin_cache_threshold, pin_powerlaw_fit]

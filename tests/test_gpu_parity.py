@@ -469,6 +469,24 @@ def test_select_ragged_and_errors(probe_data):
     assert status() == skx.SKX_EKEYRANGE
 
 
+def test_index_counts_at_ranks():
+    """Counts by transformed id, gathered on the device, equal the oracle's cnt[perm[r]]."""
+    n = 50_000
+    fk = synth.Workload(n, 1_000_003, 1.1, seed=21).fk()
+    idx = skx.skx_build_index(dev(fk), n)
+    cnt, perm, _ = oracle.build_index(fk, n)
+    ranks = np.concatenate([np.arange(10), np.random.default_rng(4).integers(0, n, 1000), [n - 1]])
+    got = skx.skx_index_counts_at_ranks(idx, ranks)
+    assert np.array_equal(got.astype(np.uint64), cnt[perm[ranks]])
+    assert skx.skx_index_counts_at_ranks(idx, np.zeros(0, dtype=np.int64)).size == 0
+    with pytest.raises(skx.SkxError):
+        skx.skx_index_counts_at_ranks(idx, [n])
+    # the fitted exponent of a Zipf(1.1) column's counts is near -1.1 over the well-sampled head
+    r = np.unique(np.geomspace(1, 2000, 40).astype(np.int64)) - 1
+    slope, _ = skx.skx_powerlaw_fit(r + 1.0, skx.skx_index_counts_at_ranks(idx, r).astype(np.float64))
+    assert abs(slope + 1.1) < 0.1
+
+
 def test_index_append_and_probe():
     n, extra = 20_000, 3_000
     w = synth.Workload(n + extra, 400_000, 1.0, seed=13, width=16)

@@ -32,6 +32,13 @@ MUTATIONS = [
     ("append_new_ids_first", "perm_out[N + j] = N + j;", "perm_out[N + j] = j;"),
     ("cache_model_no_normalisation", "double n = k * f[j] / (1.0 - fi);", "double n = k * f[j];"),
     ("cache_model_cdf_exponent", "c = 1.0 - pow(1.0 - f[i], K);", "c = 1.0 - pow(1.0 - f[i], K + 1.0);"),
+    ("threshold_counts_misses", "while (j < L && cdf[j] >= p)", "while (j < L && cdf[j] < p)"),
+    ("threshold_ignores_rows_per_line", "*t = j * (int64_t)rows_per_line;", "*t = j;"),
+    ("fit_no_log_of_x", "long double u = logl((long double)x[k])", "long double u = (long double)x[k]"),
+    ("fit_slope_sign", "long double b = ((long double)m * suv - su * sv) / den;",
+     "long double b = (su * sv - (long double)m * suv) / den;"),
+    ("fit_intercept_plus", "*intercept = (double)((sv - b * su) / (long double)m);",
+     "*intercept = (double)((sv + b * su) / (long double)m);"),
     ("thread_merge_drops_last", "for (int t = 0; t < nthreads; t++) {\n        if (jobs[t].status",
      "for (int t = 0; t < nthreads - (nthreads > 1); t++) {\n        if (jobs[t].status"),
 ]
