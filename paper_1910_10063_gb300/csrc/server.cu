@@ -6,9 +6,9 @@
 // batch with original keys in host memory.  A server thread:
 //   1. admits pending requests in arrival order while an in-flight slot and
 //      room in a fixed device arena (the memory budget) are free: the keys and
-//      measures are copied to the device and the keys are recoded through the
-//      resident rank array (the recode C' = Rank(C) of Section III-A) on a
-//      copy stream;
+//      measures are copied to the device on a copy stream that carries copies
+//      only; once copied, the keys are recoded through the resident rank array
+//      (the recode C' = Rank(C) of Section III-A) on a recode stream;
 //   2. forms a round from the remaining rows of every admitted, ready request
 //      (oldest first, up to `round_rows` rows) and runs it as one persistent
 //      batched probe (batch.cu) on a compute stream, two rounds in flight;
@@ -108,13 +108,14 @@ struct skx_server {
     skx_server_config cfg{};
     char *arena_base = nullptr;
     Arena arena;
-    cudaStream_t s_copy = nullptr, s_comp = nullptr;
+    cudaStream_t s_copy = nullptr, s_recode = nullptr, s_comp = nullptr;
     BatchDesc *d_desc[2] = {}, *h_desc[2] = {};
     uint32_t *d_tile[2] = {}, *h_tile[2] = {}, *d_counter[2] = {};
     cudaEvent_t ev_round[2] = {};
     bool round_used[2] = {false, false};
+    double round_t0[2] = {0.0, 0.0};  // host time the round was enqueued (for the deadline)
     int64_t *h_stage = nullptr;  // pinned, kMaxOut per slot
-    std::vector<cudaEvent_t> ev_ready, ev_out;
+    std::vector<cudaEvent_t> ev_copied, ev_ready, ev_out;
     std::vector<int> free_slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -163,16 +164,22 @@ bool admit_one(skx_server *s, Req *q) {
     s->free_slots.pop_back();
     q->next_row = 0;
     q->t_admit = seconds(Clock::now());
+    // only copies go on the copy stream: a kernel there would wait for SMs held by a running
+    // round, and every later copy would wait behind it.  The recode C' = Rank(C) and the
+    // cleared output follow on a recode stream once the copy is done.
     unsigned *err = device_error_word();
     cudaError_t e = cudaSuccess;
     if (q->r.F > 0) {
         e = cudaMemcpyAsync(q->d_fk, q->r.h_fk, size_t(q->r.F) * 4, cudaMemcpyHostToDevice, s->s_copy);
         if (e == cudaSuccess && q->d_m)
             e = cudaMemcpyAsync(q->d_m, q->r.h_measure, size_t(q->r.F) * 4, cudaMemcpyHostToDevice, s->s_copy);
-        if (e == cudaSuccess && s->rank) e = launch_remap(s->rank, s->N, q->d_fk, q->d_fk, q->r.F, err, s->s_copy);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(q->d_out, 0, size_t(q->nout) * 8, s->s_copy);
-    if (e == cudaSuccess) e = cudaEventRecord(s->ev_ready[q->slot], s->s_copy);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_copied[q->slot], s->s_copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->s_recode, s->ev_copied[q->slot], 0);
+    if (e == cudaSuccess && q->r.F > 0 && s->rank)
+        e = launch_remap(s->rank, s->N, q->d_fk, q->d_fk, q->r.F, err, s->s_recode);
+    if (e == cudaSuccess) e = cudaMemsetAsync(q->d_out, 0, size_t(q->nout) * 8, s->s_recode);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_ready[q->slot], s->s_recode);
     if (e != cudaSuccess) {
         cuda_status(e);
         q->state = kFailed;
@@ -181,17 +188,6 @@ bool admit_one(skx_server *s, Req *q) {
     }
     q->state = kCopying;
     return true;
-}
-
-// Waits (polling, with a deadline) for an event; false on timeout or error.
-bool wait_event(cudaEvent_t ev, double deadline_s) {
-    while (true) {
-        const cudaError_t e = cudaEventQuery(ev);
-        if (e == cudaSuccess) return true;
-        if (e != cudaErrorNotReady) return false;
-        if (seconds(Clock::now()) > deadline_s) return false;
-        std::this_thread::sleep_for(std::chrono::microseconds(5));
-    }
 }
 
 void finish(skx_server *s, Req *q, int state, skx_status st) {
@@ -236,9 +232,27 @@ void server_loop(skx_server *s) {
         int32_t max_groups = 1;
         bool any16 = false, any8 = false;
         int64_t budget = s->cfg.round_rows;
+        // the round buffer to fill next must be free; while its previous round runs the loop
+        // keeps admitting and completing requests instead of waiting (with a deadline)
+        const int rb = s->round_idx & 1;
+        bool round_free = true;
+        if (s->round_used[rb]) {
+            const cudaError_t qe = cudaEventQuery(s->ev_round[rb]);
+            if (qe == cudaErrorNotReady) {
+                round_free = false;
+                if (seconds(Clock::now()) - s->round_t0[rb] > wait_limit) {
+                    fail_all(s, SKX_ETIMEOUT);
+                    break;
+                }
+            } else if (qe != cudaSuccess) {
+                cuda_status(qe);
+                fail_all(s, SKX_ECUDA);
+                break;
+            }
+        }
         for (Req *q : s->active) {
             if (q->state == kCopying && cudaEventQuery(s->ev_ready[q->slot]) == cudaSuccess) q->state = kReady;
-            if (q->state != kReady || budget <= 0) continue;
+            if (q->state != kReady || budget <= 0 || !round_free) continue;
             const int64_t take = std::min<int64_t>(q->r.F - q->next_row, budget);
             if (take > 0) {
                 BatchDesc b{};
@@ -263,12 +277,8 @@ void server_loop(skx_server *s) {
             }
             if (q->next_row >= q->r.F) last_chunk.push_back(q);
         }
-        if (!last_chunk.empty() || !items.empty()) {
-            const int b = s->round_idx & 1;
-            if (s->round_used[b] && !wait_event(s->ev_round[b], seconds(Clock::now()) + wait_limit)) {
-                fail_all(s, SKX_ETIMEOUT);
-                break;
-            }
+        if (round_free && (!last_chunk.empty() || !items.empty())) {
+            const int b = rb;
             cudaError_t e = cudaSuccess;
             if (!items.empty()) {
                 const int32_t tile = s->cfg.tile_rows;
@@ -307,6 +317,7 @@ void server_loop(skx_server *s) {
                 break;
             }
             s->round_used[b] = true;
+            s->round_t0[b] = seconds(Clock::now());
             s->round_idx++;
             progressed = true;
         }
@@ -383,6 +394,7 @@ skx_status skx_server_create(const void *d_rows, int32_t N, int32_t row_bytes, c
     const int32_t slots = s->cfg.max_inflight;
     cudaError_t e = cudaMalloc(&s->arena_base, (size_t)s->cfg.memory_budget);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_recode, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaMalloc(&s->d_desc[b], sizeof(BatchDesc) * slots);
@@ -393,10 +405,12 @@ skx_status skx_server_create(const void *d_rows, int32_t N, int32_t row_bytes, c
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_round[b], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_stage, sizeof(int64_t) * kMaxOut * slots);
+    s->ev_copied.assign(slots, nullptr);
     s->ev_ready.assign(slots, nullptr);
     s->ev_out.assign(slots, nullptr);
     for (int i = 0; i < slots && e == cudaSuccess; ++i) {
         e = cudaEventCreateWithFlags(&s->ev_ready[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_copied[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out[i], cudaEventDisableTiming);
         s->free_slots.push_back(slots - 1 - i);
     }
@@ -525,6 +539,7 @@ void skx_server_destroy(skx_server *s) {
     }
     if (s->th.joinable()) s->th.join();
     if (s->s_copy) cudaStreamSynchronize(s->s_copy);
+    if (s->s_recode) cudaStreamSynchronize(s->s_recode);
     if (s->s_comp) cudaStreamSynchronize(s->s_comp);
     for (auto &kv : s->reqs) delete kv.second;
     for (int b = 0; b < 2; ++b) {
@@ -537,11 +552,14 @@ void skx_server_destroy(skx_server *s) {
     }
     for (cudaEvent_t e : s->ev_ready)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->ev_copied)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : s->ev_out)
         if (e) cudaEventDestroy(e);
     if (s->h_stage) cudaFreeHost(s->h_stage);
     if (s->arena_base) cudaFree(s->arena_base);
     if (s->s_copy) cudaStreamDestroy(s->s_copy);
+    if (s->s_recode) cudaStreamDestroy(s->s_recode);
     if (s->s_comp) cudaStreamDestroy(s->s_comp);
     delete s;
 }
