@@ -443,7 +443,12 @@ def run_ours(a, rank, world, local_rank):
             cnt1 = torch.empty(1, dtype=torch.int64, device=dev)
             entry["q2_select_plain_ms"] = t_ms(lambda: skx.skx_select(bits_p, a.n, fk_s, offs, cnt1))
             entry["q2_select_remapped_ms"] = t_ms(lambda: skx.skx_select(bits_r, a.n, fk2, offs, cnt1))
-            del offs, cnt_buf
+            # Q1 materialisation of attribute payload0 (column 2): the paper's main microbenchmark query
+            q1_out = offs  # int32[F]
+            entry["q1_materialize_plain_ms"] = t_ms(lambda: skx.skx_materialize(w.dim, fk_s, 2, out=q1_out))
+            entry["q1_materialize_remapped_ms"] = t_ms(lambda: skx.skx_materialize(dim2, fk2, 2, out=q1_out))
+            entry["speedup_q1"] = round(entry["q1_materialize_plain_ms"] / entry["q1_materialize_remapped_ms"], 3)
+            del offs, cnt_buf, q1_out
             entry["speedup_remapped_vs_plain"] = round(entry["plain"]["ms"] / entry["remapped"]["ms"], 3)
             entry["speedup_columns16"] = round(entry["plain_columns16"]["ms"] / entry["remapped_columns16"]["ms"], 3)
             entry["speedup_query8"] = round(entry["plain_query8"]["ms"] / entry["remapped_query8"]["ms"], 3)
@@ -635,10 +640,18 @@ def run_cachefit(a):
         t_rem = timed(lambda: skx.skx_probe_aggregate(dim2, fk2, measure, q, tuning=tr))
         a_ = skx.skx_probe_aggregate(w.dim, w.fk, measure, q, tuning=tp).cpu()
         b_ = skx.skx_probe_aggregate(dim2, fk2, measure, q, tuning=tr).cpu()
+        # Q1, the paper's microbenchmark query: materialise payload0 per fact row, both layouts
+        q1a = torch.empty(F, dtype=torch.int32, device=dev)
+        q1b = torch.empty(F, dtype=torch.int32, device=dev)
+        t_q1p = timed(lambda: skx.skx_materialize(w.dim, w.fk, 2, out=q1a))
+        t_q1r = timed(lambda: skx.skx_materialize(dim2, fk2, 2, out=q1b))
+        q1_same = bool(torch.equal(q1a, q1b))
+        del q1a, q1b
         rows.append({"N": n, "table_bytes": n * a.width * 4, "build_ms": t_build, "remap_ms": t_remap,
                      "reorder_ms": t_reorder, "probe_plain_ms": t_plain, "probe_remapped_ms": t_rem,
                      "speedup": round(t_plain / t_rem, 3), "identical": bool(torch.equal(a_, b_)),
-                     "remapped_tuning_hot_keys": tr.hot_keys})
+                     "q1_plain_ms": t_q1p, "q1_remapped_ms": t_q1r, "q1_speedup": round(t_q1p / t_q1r, 3),
+                     "q1_identical": q1_same, "remapped_tuning_hot_keys": tr.hot_keys})
         if nm == 64:
             # drift: 10% of the ranks re-shuffled; the old index stays in use vs a rebuild
             r2d = synth.drift_rank_to_id(w.r2id_host, a.seed, 0.1)

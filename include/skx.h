@@ -196,6 +196,19 @@ skx_status skx_remap(const skx_index *idx, const int32_t *d_fk_in, int32_t *d_fk
                      void *stream);
 
 /* ------------------------------------------------------------------------
+ * Materialisation, query Q1 (Sections I and IV-A): d_out[i] = column col
+ * (int32) of row d_fk[i] of d_rows (N rows of row_bytes bytes, row-major,
+ * 4-byte aligned, row_bytes a multiple of 4), for i < F, int32.  Works on
+ * either layout: (plain rows, original keys) or (reordered rows, recoded
+ * keys) give the same d_out.  Keys outside [0, N) give 0 and raise
+ * SKX_EKEYRANGE at skx_stream_status.  d_out must not overlap the inputs.
+ * Errors: SKX_EINVAL (null pointer with F > 0, N < 1, bad row_bytes, col
+ * outside the row, F >= 2^32, misaligned pointers), SKX_ENOMEM, SKX_ECUDA.
+ * ------------------------------------------------------------------------ */
+skx_status skx_materialize(const void *d_rows, int32_t N, int32_t row_bytes, int32_t col, const int32_t *d_fk,
+                           int64_t F, int32_t *d_out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Permuted copy of the dimension table (Section III-B):
  * row r of d_rows_out = row perm[r] of d_rows_in, row_bytes bytes each
  * (a multiple of 4).  Input and output must not overlap.

@@ -15,6 +15,8 @@ Improved Query Performance" (ICDE 2020, arXiv 1910.10063):
 * ``build_index``        the three steps above (Section III-A)
 * ``remap``              recode C'[i] = Rank(C[i]) (Section III-A, step 3)
 * ``reorder``            permuted copy of the dimension rows (Section III-B)
+* ``materialize``        Q1: the referenced dimension attribute per fact row
+                         (Sections I, IV-A)
 * ``probe``              FK gather + filter + aggregation (Sections I, IV-A;
                          threads over fact chunks with independent buffers,
                          Section IV-C)
@@ -97,9 +99,10 @@ def _declare(lib):
     lib.orc_cache_hit_rate.argtypes = [P, i64, i64, P, P]
     lib.orc_cache_threshold.argtypes = [P, i64, i64, ctypes.c_double, i32, P]
     lib.orc_powerlaw_fit.argtypes = [P, P, i64, P, P]
+    lib.orc_materialize.argtypes = [P, i32, i32, i32, P, i64, P]
     for f in ("orc_histogram", "orc_sort_by_frequency", "orc_invert", "orc_build_index",
               "orc_remap", "orc_reorder", "orc_probe", "orc_topk_counts", "orc_select", "orc_index_append",
-              "orc_cache_hit_rate", "orc_cache_threshold", "orc_powerlaw_fit"):
+              "orc_cache_hit_rate", "orc_cache_threshold", "orc_powerlaw_fit", "orc_materialize"):
         getattr(lib, f).restype = cint
     return lib
 
@@ -271,3 +274,17 @@ def powerlaw_fit(x, y, lib=None):
     if st:
         raise OracleError(st, "powerlaw_fit")
     return float(out[0]), float(out[1])
+
+
+def materialize(rows, fk, col: int, lib=None) -> np.ndarray:
+    """Q1: int32 out[i] = rows[fk[i]][col] (rows: int32[N, W])."""
+    lib = lib or load()
+    rows = _c(rows, np.int32)
+    if rows.ndim != 2:
+        raise ValueError("rows must be int32[N, W]")
+    fk = _c(fk, np.int32)
+    out = np.zeros(fk.shape[0], dtype=np.int32)
+    st = lib.orc_materialize(_ptr(rows), rows.shape[0], rows.shape[1], col, _ptr(fk), fk.shape[0], _ptr(out))
+    if st:
+        raise OracleError(st, "materialize")
+    return out

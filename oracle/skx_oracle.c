@@ -507,3 +507,19 @@ int orc_powerlaw_fit(const double *x, const double *y, int64_t n, double *slope,
     *intercept = (double)((sv - b * su) / (long double)m);
     return ORC_OK;
 }
+
+/* Q1 materialisation (Sections I and IV-A): the attribute col of the
+ * dimension row each fact row references, out[i] = rows[fk[i]][col]. */
+int orc_materialize(const int32_t *rows, int32_t N, int32_t row_words, int32_t col, const int32_t *fk, int64_t F,
+                    int32_t *out)
+{
+    if (!rows || N < 1 || row_words < 1 || col < 0 || col >= row_words || F < 0 || (F > 0 && (!fk || !out)))
+        return ORC_EINVAL;
+    for (int64_t i = 0; i < F; i++) {
+        int32_t v = fk[i];
+        if (v < 0 || v >= N)
+            return ORC_EKEY;
+        out[i] = rows[(int64_t)v * row_words + col];
+    }
+    return ORC_OK;
+}

@@ -133,6 +133,7 @@ def lib():
             L.skx_index_destroy.argtypes = [P]; L.skx_index_destroy.restype = None
             L.skx_remap.argtypes = [P, P, P, i64, P]; L.skx_remap.restype = st
             L.skx_reorder.argtypes = [P, P, P, i32, i32, P]; L.skx_reorder.restype = st
+            L.skx_materialize.argtypes = [P, i32, i32, i32, P, i64, P, P]; L.skx_materialize.restype = st
             L.skx_reorder_columns.argtypes = [P, P, i32, i32, P, i32, P, P]; L.skx_reorder_columns.restype = st
             L.skx_reorder_query.argtypes = [P, P, i32, i32, ctypes.POINTER(Query), P, P]
             L.skx_reorder_query.restype = st
@@ -355,6 +356,19 @@ def skx_reorder(index: Index, rows_in, rows_out, stream=None):
     _check(lib().skx_reorder(index._h, _dptr(rows_in, "rows_in"), _dptr(rows_out, "rows_out"), rows_in.shape[0],
                              _row_bytes(rows_in), _stream(stream)), "skx_reorder")
     return rows_out
+
+
+def skx_materialize(rows, fk, col: int, out=None, stream=None):
+    """Q1: int32 out[i] = rows[fk[i], col] on the device (either layout)."""
+    import torch
+    if out is None:
+        out = torch.empty(fk.numel(), dtype=torch.int32, device=fk.device)
+    if out.numel() < fk.numel():
+        raise ValueError("out is shorter than fk")
+    _check(lib().skx_materialize(_dptr(rows, "rows"), rows.shape[0], _row_bytes(rows), int(col),
+                                 _dptr(fk, "fk", torch.int32), fk.numel(), _dptr(out, "out", torch.int32),
+                                 _stream(stream)), "skx_materialize")
+    return out
 
 
 def skx_reorder_columns(index: Index | None, rows_in, cols, out=None, stream=None):

@@ -361,6 +361,18 @@ skx_status skx_remap(const skx_index *idx, const int32_t *d_fk_in, int32_t *d_fk
     return SKX_OK;
 }
 
+skx_status skx_materialize(const void *d_rows, int32_t N, int32_t row_bytes, int32_t col, const int32_t *d_fk,
+                           int64_t F, int32_t *d_out, void *stream) {
+    if (!d_rows || N < 1 || row_bytes <= 0 || row_bytes % 4 != 0 || col < 0 || col >= row_bytes / 4 || F < 0 ||
+        F >= (int64_t(1) << 32) || (F > 0 && (!d_fk || !d_out)))
+        return SKX_EINVAL;
+    if (!valid_stream_ptrs(d_rows) || !valid_stream_ptrs(d_fk) || !valid_stream_ptrs(d_out)) return SKX_EINVAL;
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    SKX_CUDA_TRY(launch_materialize(d_rows, N, row_bytes, col, d_fk, F, d_out, err, static_cast<cudaStream_t>(stream)));
+    return SKX_OK;
+}
+
 skx_status skx_reorder(const skx_index *idx, const void *d_rows_in, void *d_rows_out, int32_t N, int32_t row_bytes,
                        void *stream) {
     if (!idx || N != idx->N || row_bytes <= 0 || row_bytes % 4 != 0 || !d_rows_in || !d_rows_out) return SKX_EINVAL;

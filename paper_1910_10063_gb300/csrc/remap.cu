@@ -4,6 +4,8 @@
 //                                              (Section III-A)
 //   reorder  rows_out[r] = rows_in[perm[r]]    permuted copy of the dimension
 //                                              rows (Section III-B)
+//   materialize  out[i] = rows[fk[i]][col]     query Q1 over either layout
+//                                              (Sections I, IV-A)
 //
 // GB300 design: remap streams the fact column with 16-byte loads and stores
 // marked L2 evict-first, so that rank[] (4 B per id) stays L2-resident for
@@ -83,6 +85,75 @@ __global__ void __launch_bounds__(kRemapBlock)
                    unsigned *err) {
     for (int64_t i = int64_t(blockIdx.x) * kRemapBlock + threadIdx.x; i < F; i += int64_t(gridDim.x) * kRemapBlock)
         out[i] = remap_one(in[i], rank, N, err);
+}
+
+// Q1 materialisation (Sections I, IV-A): out[i] = column col of row fk[i]
+// (int32).  The fact keys stream with 16-byte evict-first loads, one 4-byte
+// gather per key, 16-byte evict-first stores; the next vectors' keys are in
+// flight while this one's gathers resolve.  Keys outside [0, N) give 0 and
+// are flagged.
+__device__ __forceinline__ int32_t gather_col(const int32_t *__restrict__ rows, int64_t words, int32_t col, int32_t k,
+                                              int32_t N, unsigned *err) {
+    if ((uint32_t)k < (uint32_t)N) return __ldg(rows + int64_t(k) * words + col);
+    raise_error(err, kErrKeyRange);
+    return 0;
+}
+
+__global__ void __launch_bounds__(kRemapBlock)
+    k_materialize(const int32_t *__restrict__ rows, int64_t words, int32_t col, int32_t N,
+                  const int32_t *__restrict__ fk, int32_t *__restrict__ out, int64_t F, int64_t head,
+                  unsigned *err) {
+    const uint64_t pol = policy_evict_first();
+    const int4 *vin = reinterpret_cast<const int4 *>(fk + head);
+    int4 *vout = reinterpret_cast<int4 *>(out + head);
+    const int64_t nvec = (F - head) >> 2;
+    const int64_t tid = int64_t(blockIdx.x) * kRemapBlock + threadIdx.x;
+    const int64_t nthr = int64_t(gridDim.x) * kRemapBlock;
+    int4 nk[kRemapUnroll];
+#pragma unroll
+    for (int u = 0; u < kRemapUnroll; ++u) {
+        const int64_t i = tid + u * nthr;
+        if (i < nvec) nk[u] = ld_stream16(vin + i, pol);
+    }
+    for (int64_t base = tid; base < nvec; base += nthr * kRemapUnroll) {
+        int4 k[kRemapUnroll], r[kRemapUnroll];
+#pragma unroll
+        for (int u = 0; u < kRemapUnroll; ++u) k[u] = nk[u];
+#pragma unroll
+        for (int u = 0; u < kRemapUnroll; ++u) {
+            if (base + u * nthr < nvec) {
+                r[u].x = gather_col(rows, words, col, k[u].x, N, err);
+                r[u].y = gather_col(rows, words, col, k[u].y, N, err);
+                r[u].z = gather_col(rows, words, col, k[u].z, N, err);
+                r[u].w = gather_col(rows, words, col, k[u].w, N, err);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kRemapUnroll; ++u) {
+            const int64_t i = base + (kRemapUnroll + u) * nthr;
+            if (i < nvec) nk[u] = ld_stream16(vin + i, pol);
+        }
+#pragma unroll
+        for (int u = 0; u < kRemapUnroll; ++u) {
+            const int64_t i = base + u * nthr;
+            if (i < nvec) st_stream16(vout + i, r[u], pol);
+        }
+    }
+    if (tid < 8) {  // unaligned head (< 4) and ragged tail (< 4)
+        const int64_t tail0 = head + (nvec << 2);
+        int64_t idx = -1;
+        if (tid < head) idx = tid;
+        else if (tid >= 4 && tail0 + (tid - 4) < F) idx = tail0 + (tid - 4);
+        if (idx >= 0) out[idx] = gather_col(rows, words, col, fk[idx], N, err);
+    }
+}
+
+// fk and out at different offsets mod 16 bytes: plain 4-byte path
+__global__ void __launch_bounds__(kRemapBlock)
+    k_materialize_scalar(const int32_t *__restrict__ rows, int64_t words, int32_t col, int32_t N,
+                         const int32_t *__restrict__ fk, int32_t *__restrict__ out, int64_t F, unsigned *err) {
+    for (int64_t i = int64_t(blockIdx.x) * kRemapBlock + threadIdx.x; i < F; i += int64_t(gridDim.x) * kRemapBlock)
+        out[i] = gather_col(rows, words, col, fk[i], N, err);
 }
 
 template <typename Chunk>
@@ -175,6 +246,27 @@ cudaError_t launch_remap(const int32_t *d_rank, int32_t N, const int32_t *d_in, 
         k_remap<true><<<grid, kRemapBlock, 0, st>>>(d_rank, N, d_in, d_out, F, head, d_err);
     else
         k_remap<false><<<grid, kRemapBlock, 0, st>>>(d_rank, N, d_in, d_out, F, head, d_err);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_materialize(const void *d_rows, int32_t N, int32_t row_bytes, int32_t col, const int32_t *d_fk,
+                               int64_t F, int32_t *d_out, unsigned *d_err, cudaStream_t st) {
+    if (F <= 0) return cudaSuccess;
+    const int32_t *rows = static_cast<const int32_t *>(d_rows);
+    const int64_t words = row_bytes / 4;
+    const uintptr_t ai = reinterpret_cast<uintptr_t>(d_fk) & 15u, ao = reinterpret_cast<uintptr_t>(d_out) & 15u;
+    if (ai != ao) {
+        k_materialize_scalar<<<grid_for(F, kRemapBlock, 4), kRemapBlock, 0, st>>>(rows, words, col, N, d_fk, d_out, F,
+                                                                                  d_err);
+        note_launches(1);
+        return cudaGetLastError();
+    }
+    const int64_t mis = (int64_t)(ai >> 2);
+    const int64_t head = mis ? (F < 4 - mis ? F : 4 - mis) : 0;
+    const int64_t nvec = (F - head) >> 2;
+    const int grid = grid_for((nvec + kRemapUnroll - 1) / kRemapUnroll, kRemapBlock, 2048 / kRemapBlock);
+    k_materialize<<<grid, kRemapBlock, 0, st>>>(rows, words, col, N, d_fk, d_out, F, head, d_err);
     note_launches(1);
     return cudaGetLastError();
 }

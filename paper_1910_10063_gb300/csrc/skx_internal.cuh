@@ -179,6 +179,8 @@ cudaError_t launch_remap(const int32_t *d_rank, int32_t N, const int32_t *d_in, 
                          unsigned *d_err, cudaStream_t st);
 cudaError_t launch_reorder(const int32_t *d_perm, int32_t N, const void *d_in, void *d_out, int32_t row_bytes,
                            cudaStream_t st);
+cudaError_t launch_materialize(const void *d_rows, int32_t N, int32_t row_bytes, int32_t col, const int32_t *d_fk,
+                               int64_t F, int32_t *d_out, unsigned *d_err, cudaStream_t st);
 cudaError_t launch_reorder_columns(const int32_t *d_perm, int32_t N, const void *d_in, int32_t row_bytes,
                                    const int32_t *cols, int32_t ncols, void *d_out, cudaStream_t st);
 cudaError_t launch_reorder_query(const int32_t *d_perm, int32_t N, const void *d_in, int32_t row_bytes,

@@ -398,7 +398,31 @@ def pin_powerlaw_fit(lib):
         raise AssertionError("degenerate fit accepted")
 
 
+def pin_materialize(lib):
+    # brute force: the attribute of the referenced row, for every fact row
+    rng = np.random.default_rng(31)
+    rows = rng.integers(-1000, 1000, size=(57, 5), dtype=np.int32)
+    fk = rng.integers(0, 57, size=1001).astype(np.int32)
+    for col in range(5):
+        want = np.array([int(rows[int(k), col]) for k in fk], dtype=np.int32)
+        assert np.array_equal(oracle.materialize(rows, fk, col, lib=lib), want)
+    # Fig. 2 style check of layout invariance: reorder the rows and recode the keys with the
+    # index, and every fact row still sees the same attribute
+    cnt, perm, rank = oracle.build_index(fk, 57, lib=lib)
+    rows2 = rows[perm]
+    fk2 = rank[fk].astype(np.int32)
+    for col in (0, 3):
+        assert np.array_equal(oracle.materialize(rows2, fk2, col, lib=lib), oracle.materialize(rows, fk, col, lib=lib))
+    assert oracle.materialize(rows, np.zeros(0, dtype=np.int32), 0, lib=lib).size == 0
+    for bad_fk, bad_col in ((np.array([0, 57], dtype=np.int32), 0), (np.array([-1], dtype=np.int32), 0), (fk, 5)):
+        try:
+            oracle.materialize(rows, bad_fk, bad_col, lib=lib)
+        except oracle.OracleError:
+            continue
+        raise AssertionError("invalid materialisation accepted")
+
+
 ALL_PINS = [pin_fig2_example, pin_histogram, pin_sort_by_frequency, pin_invert, pin_remap,
             pin_reorder, pin_probe_brute_force, pin_probe_closed_forms, pin_probe_wraparound,
             pin_probe_layout_invariance, pin_probe_errors, pin_topk_counts, pin_select, pin_index_append,
-            pin_cache_model, pin_cache_threshold, pin_powerlaw_fit]
+            pin_cache_model, pin_cache_threshold, pin_powerlaw_fit, pin_materialize]

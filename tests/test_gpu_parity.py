@@ -469,6 +469,40 @@ def test_select_ragged_and_errors(probe_data):
     assert status() == skx.SKX_EKEYRANGE
 
 
+@pytest.mark.parametrize("f", [0, 1, 3, 5, 4097, 300_001])
+@pytest.mark.parametrize("off_fk,off_out", [(0, 0), (1, 1), (2, 0), (3, 1)])
+def test_materialize_parity(f, off_fk, off_out):
+    """Q1 on the plain layout and on the remapped one, against the oracle; unaligned and
+    mismatched offsets (vector and scalar paths), ragged tails."""
+    w = synth.Workload(20_000, f, 1.0, seed=29, width=16)
+    fk, dim = w.fk(), w.dim()
+    want = oracle.materialize(dim, fk, 2)
+    out_buf = torch.zeros(f + off_out + 8, dtype=torch.int32, device=DEV)
+    out = out_buf[off_out:off_out + f]
+    skx.skx_materialize(dev(dim), offset_view(fk, off_fk), 2, out=out)
+    assert status() == skx.SKX_OK
+    assert np.array_equal(out.cpu().numpy(), want)
+    if f:
+        idx = skx.skx_build_index(dev(fk), 20_000)
+        _, perm, rank = oracle.build_index(fk, 20_000)
+        fk2 = rank[fk].astype(np.int32)
+        got = skx.skx_materialize(dev(dim[perm]), dev(fk2), 2).cpu().numpy()
+        assert np.array_equal(got, want)                                  # layout invariance
+
+
+def test_materialize_errors_and_columns():
+    dim = np.arange(40, dtype=np.int32).reshape(10, 4)
+    fk = np.array([0, 9, 10, 3, -1, 5], dtype=np.int32)
+    out = skx.skx_materialize(dev(dim), dev(fk), 3).cpu().numpy()
+    assert status() == skx.SKX_EKEYRANGE
+    assert np.array_equal(out, [3, 39, 0, 15, 0, 23])
+    for col in range(4):
+        ok = np.array([0, 9, 3, 5], dtype=np.int32)
+        assert np.array_equal(skx.skx_materialize(dev(dim), dev(ok), col).cpu().numpy(), dim[ok, col])
+    with pytest.raises(skx.SkxError):
+        skx.skx_materialize(dev(dim), dev(fk), 4)
+
+
 def test_index_counts_at_ranks():
     """Counts by transformed id, gathered on the device, equal the oracle's cnt[perm[r]]."""
     n = 50_000

@@ -39,6 +39,9 @@ MUTATIONS = [
      "long double b = (su * sv - (long double)m * suv) / den;"),
     ("fit_intercept_plus", "*intercept = (double)((sv - b * su) / (long double)m);",
      "*intercept = (double)((sv + b * su) / (long double)m);"),
+    ("materialize_wrong_stride", "out[i] = rows[(int64_t)v * row_words + col];", "out[i] = rows[(int64_t)v + col];"),
+    ("materialize_no_recode_of_key", "int32_t v = fk[i];\n        if (v < 0 || v >= N)\n            return ORC_EKEY;\n        out[i]",
+     "int32_t v = (int32_t)(i % N);\n        if (v < 0 || v >= N)\n            return ORC_EKEY;\n        out[i]"),
     ("thread_merge_drops_last", "for (int t = 0; t < nthreads; t++) {\n        if (jobs[t].status",
      "for (int t = 0; t < nthreads - (nthreads > 1); t++) {\n        if (jobs[t].status"),
 ]
