@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include "skx_internal.cuh"
 
@@ -71,6 +73,30 @@ cudaStream_t copy_stream() {
 }  // namespace
 
 void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+namespace {
+std::set<std::pair<int, const void *>> g_smem_set;  // (device, kernel) with the limit raised
+}  // namespace
+
+cudaError_t set_smem_limit_once(const void *kernel, int dynamic_bytes) {
+    const int d = current_device();
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_smem_set.count({d, kernel})) return cudaSuccess;
+    }
+    if (dynamic_bytes < 0) {
+        cudaFuncAttributes fa{};
+        const cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+        if (e != cudaSuccess) return e;
+        dynamic_bytes = device_max_smem_optin() - (int)fa.sharedSizeBytes;
+    }
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dynamic_bytes);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_smem_set.insert({d, kernel});
+    }
+    return e;
+}
 
 skx_status cuda_status(cudaError_t e) {
     snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));

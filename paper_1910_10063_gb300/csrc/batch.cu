@@ -249,18 +249,10 @@ cudaError_t launch_batch_items(const BatchDesc *d_desc, const uint32_t *d_tile_s
     const int block = t.block_threads;
     int per_sm = 0;
     auto go = [&](auto kern) -> cudaError_t {
-        static int configured = -1;
-        if (configured != optin) {
-            cudaFuncAttributes fa{};
-            cudaError_t e2 = cudaFuncGetAttributes(&fa, kern);
-            if (e2 != cudaSuccess) return e2;
-            // dynamic + static shared memory must fit the per-block limit
-            e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      optin - (int)fa.sharedSizeBytes);
-            if (e2 != cudaSuccess) return e2;
-            configured = optin;
-        }
-        cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+        // dynamic + static shared memory must fit the per-block limit
+        cudaError_t e2 = set_smem_limit_once(reinterpret_cast<const void *>(kern), -1);
+        if (e2 != cudaSuccess) return e2;
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
         if (e2 != cudaSuccess) return e2;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         if (t.ctas_per_sm > 0 && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;

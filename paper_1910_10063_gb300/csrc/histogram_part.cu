@@ -577,22 +577,15 @@ cudaError_t launch_histogram_partitioned(const int32_t *d_fk, int64_t F, int32_t
     const size_t smem_a = size_t(p.B + 1) * 4;
     const size_t smem_c = scatter_smem_words(p.B) * 4;
     const size_t smem_d = (size_t(kBkt) + p.B + 1) * 4;
-    static int configured = -1;
-    const int optin = device_max_smem_optin();
-    if (configured != optin) {
-        cudaError_t e = cudaFuncSetAttribute(k_part_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (kMaxBuckets + 1) * 4);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_part_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(scatter_smem_words(kMaxBuckets) * 4));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_part_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)((kBkt + kMaxBuckets + 1) * 4));
-        if (e != cudaSuccess) return e;
-        configured = optin;
-    }
+    cudaError_t e = set_smem_limit_once(reinterpret_cast<const void *>(k_part_count), (kMaxBuckets + 1) * 4);
+    if (e == cudaSuccess)
+        e = set_smem_limit_once(reinterpret_cast<const void *>(k_part_scatter),
+                                (int)(scatter_smem_words(kMaxBuckets) * 4));
+    if (e == cudaSuccess)
+        e = set_smem_limit_once(reinterpret_cast<const void *>(k_part_hist), (int)((kBkt + kMaxBuckets + 1) * 4));
+    if (e != cudaSuccess) return e;
     k_part_count<<<G, kPBlock, smem_a, st>>>(s, mat, queue, d_err, run_if_set);
-    cudaError_t e = exclusive_scan_u32(mat, p.L, bsum, st, run_if_set);
+    e = exclusive_scan_u32(mat, p.L, bsum, st, run_if_set);
     if (e != cudaSuccess) return e;
     k_part_scatter<<<G, kPBlock, smem_c, st>>>(s, mat, part, run_if_set);
     k_part_hist<<<device_sm_count(), kDBlock, smem_d, st>>>(part, mat, p.B, G, N, queue, d_cnt, run_if_set);
@@ -606,14 +599,8 @@ cudaError_t launch_count_choice(const int32_t *d_fk, int64_t F, int32_t N, void 
     const PartLayout p = part_layout(N, F);
     if (!d_scratch || scratch_bytes < p.total) return cudaErrorInvalidValue;
     uint32_t *f = reinterpret_cast<uint32_t *>(static_cast<char *>(d_scratch) + p.off_flag);
-    static int configured = -1;
-    const int optin = device_max_smem_optin();
-    if (configured != optin) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_count_choose, cudaFuncAttributeMaxDynamicSharedMemorySize, kSampleSlots * 8);
-        if (e != cudaSuccess) return e;
-        configured = optin;
-    }
+    const cudaError_t e = set_smem_limit_once(reinterpret_cast<const void *>(k_count_choose), kSampleSlots * 8);
+    if (e != cudaSuccess) return e;
     k_count_choose<<<1, kChooseBlock, kSampleSlots * 8, st>>>(d_fk, F, N, f);
     note_launches(1);
     *flag = f;

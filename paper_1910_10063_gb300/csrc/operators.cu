@@ -172,17 +172,10 @@ skx_status skx_topk_counts(const int32_t *d_fk, int64_t F, int32_t k, int64_t *d
     const int64_t head = mis ? (F < 4 - mis ? F : 4 - mis) : 0;
     unsigned long long *out = reinterpret_cast<unsigned long long *>(d_out);
     auto go = [&](auto kern) -> cudaError_t {
-        static int configured = -1;
-        if (configured != optin) {
-            cudaFuncAttributes fa{};
-            cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-            if (e != cudaSuccess) return e;
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-            if (e != cudaSuccess) return e;
-            configured = optin;
-        }
+        cudaError_t e = set_smem_limit_once(reinterpret_cast<const void *>(kern), -1);
+        if (e != cudaSuccess) return e;
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOpBlock, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOpBlock, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         kern<<<grid_cap(((F - head) >> 2) + 1, per_sm), kOpBlock, smem, st>>>(d_fk, F, head, k, out);

@@ -154,19 +154,11 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
 template <int AGG, int PATH, bool GSMEM, int UNROLL>
 cudaError_t launch_one(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st) {
     auto kern = k_probe<AGG, PATH, GSMEM, UNROLL>;
-    static int configured_smem = -1;  // per instantiation; the device limit is the same for all GB300s
-    const int want = device_max_smem_optin();
-    if (configured_smem != want) {
-        cudaFuncAttributes fa{};
-        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-        if (e != cudaSuccess) return e;
-        // dynamic + static shared memory must fit the per-block limit
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, want - (int)fa.sharedSizeBytes);
-        if (e != cudaSuccess) return e;
-        configured_smem = want;
-    }
+    // dynamic + static shared memory must fit the per-block limit
+    cudaError_t e = set_smem_limit_once(reinterpret_cast<const void *>(kern), -1);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t.block_threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t.block_threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (t.ctas_per_sm > 0 && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;

@@ -21,6 +21,10 @@ unsigned *device_error_word();                  // per-device word (lazily alloc
 int device_sm_count();                          // SMs of the current device
 int device_max_smem_optin();                    // max dynamic smem per block (opt-in)
 void note_launches(int n);                      // adds to the process-wide kernel-launch counter
+// Raises a kernel's dynamic shared-memory limit on the current device, once per (device,
+// kernel): the attribute belongs to each device's context.  dynamic_bytes < 0 asks for the
+// device's opt-in limit minus the kernel's static shared memory.
+cudaError_t set_smem_limit_once(const void *kernel, int dynamic_bytes);
 
 #define SKX_CUDA_TRY(expr)                                  \
     do {                                                    \
