@@ -88,18 +88,23 @@ __global__ void __launch_bounds__(kSortBlock)
     const uint32_t tile = blockIdx.x;
     const uint32_t base = tile * kTile + warp * (32 * kRounds);
     if (tile * kTile < n) {  // tiles past the end (heavy passes) publish zero counts
-#pragma unroll 4
+        // all of the warp's loads first, so their latencies overlap; then the ranking rounds
+        uint32_t dig[kRounds];
+#pragma unroll
         for (int r = 0; r < kRounds; ++r) {
             const uint32_t i = base + r * 32 + lane;
-            const bool valid = i < n;
-            uint32_t d = kBins;  // sentinel for lanes past the end
-            if (valid) {
+            dig[r] = kBins;  // sentinel for lanes past the end
+            if (i < n) {
                 uint32_t key, val;
                 load_key<SRC>(cnt, keys_in, vals_in, i, key, val);
-                d = (key >> shift) & (kBins - 1);
+                dig[r] = (key >> shift) & (kBins - 1);
             }
+        }
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const uint32_t d = dig[r];
             const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (valid && lane == (unsigned)(__ffs(peers) - 1)) s_cnt[warp][d] += __popc(peers);
+            if (d < (uint32_t)kBins && lane == (unsigned)(__ffs(peers) - 1)) s_cnt[warp][d] += __popc(peers);
         }
     }
     __syncthreads();
@@ -223,17 +228,19 @@ __global__ void __launch_bounds__(kSortBlock)
 
     const uint32_t base = tile * kTile + warp * (32 * kRounds);
     uint32_t key[kRounds], val[kRounds], loc[kRounds];
+    // all of the warp's loads first, so their latencies overlap; then the ranking rounds
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        key[r] = 0;
+        val[r] = 0;
+        if (i < n) load_key<SRC>(cnt, keys_in, vals_in, i, key[r], val[r]);
+    }
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const uint32_t i = base + r * 32 + lane;
         const bool valid = i < n;
-        key[r] = 0;
-        val[r] = 0;
-        uint32_t d = kBins;
-        if (valid) {
-            load_key<SRC>(cnt, keys_in, vals_in, i, key[r], val[r]);
-            d = (key[r] >> shift) & (kBins - 1);
-        }
+        const uint32_t d = valid ? ((key[r] >> shift) & (kBins - 1)) : kBins;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         uint32_t before = 0;
