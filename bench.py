@@ -340,7 +340,7 @@ def run_ours(a, rank, world, local_rank):
     row_b = a.width * 4
     alg = {"count": 4 * a.f + 4 * a.n, "sort": 12 * a.n, "remap": 8 * a.f + 4 * a.n,
            "reorder": 2 * row_b * a.n + 4 * a.n, "probe": 8 * a.f + 16 * D}
-    kernel_of = {"count": count_kernels(w.fk, a.n, a.f, a.count_method), "sort": "k_radix_*", "remap": "k_remap", "reorder": "k_reorder",
+    kernel_of = {"count": count_kernels(w.fk, a.n, a.f, a.count_method), "sort": "k_radix_*", "remap": "k_remap", "reorder": "k_reorder16",
                  "probe": "k_probe"}
     stage_avg = {s: statistics.mean(v) for s, v in stage_ms.items()}
     stage_rep = {s: {"ms": round(stage_avg[s], 4), "alg_bytes": int(alg[s]),

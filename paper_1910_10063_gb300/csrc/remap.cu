@@ -156,6 +156,28 @@ __global__ void __launch_bounds__(kRemapBlock)
         out[i] = gather_col(rows, words, col, fk[i], N, err);
 }
 
+// 16-byte read of a source row through the read-only path with the L2 told to
+// fetch 64 bytes (the row) rather than a longer line
+__device__ __forceinline__ int4 ld_row16_p64(const int4 *p) {
+    int4 v;
+    asm volatile("ld.global.nc.L2::64B.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__global__ void __launch_bounds__(512)
+    k_reorder16(const int32_t *__restrict__ perm, int32_t N, const int4 *__restrict__ in, int4 *__restrict__ out,
+                int32_t chunks_per_row) {
+    const int64_t total = int64_t(N) * chunks_per_row;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < total; j += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = j / chunks_per_row;
+        const int64_t c = j - r * chunks_per_row;
+        const int32_t src = __ldg(perm + r);
+        if ((uint32_t)src < (uint32_t)N) out[j] = ld_row16_p64(in + int64_t(src) * chunks_per_row + c);
+    }
+}
+
 template <typename Chunk>
 __global__ void __launch_bounds__(512)
     k_reorder(const int32_t *__restrict__ perm, int32_t N, const Chunk *__restrict__ in, Chunk *__restrict__ out,
@@ -307,8 +329,8 @@ cudaError_t launch_reorder(const int32_t *d_perm, int32_t N, const void *d_in, v
     if (N <= 0) return cudaSuccess;
     if (row_bytes % 16 == 0 && aligned16(d_in) && aligned16(d_out)) {
         const int32_t w = row_bytes / 16;
-        k_reorder<int4><<<grid_for(int64_t(N) * w, 512, 4), 512, 0, st>>>(
-            d_perm, N, static_cast<const int4 *>(d_in), static_cast<int4 *>(d_out), w);
+        k_reorder16<<<grid_for(int64_t(N) * w, 512, 4), 512, 0, st>>>(d_perm, N, static_cast<const int4 *>(d_in),
+                                                                      static_cast<int4 *>(d_out), w);
     } else {
         const int32_t w = row_bytes / 4;
         k_reorder<int32_t><<<grid_for(int64_t(N) * w, 512, 4), 512, 0, st>>>(
