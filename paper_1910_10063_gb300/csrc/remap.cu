@@ -156,8 +156,9 @@ __global__ void __launch_bounds__(kRemapBlock)
         out[i] = gather_col(rows, words, col, fk[i], N, err);
 }
 
-// 16-byte read of a source row through the read-only path with the L2 told to
-// fetch 64 bytes (the row) rather than a longer line
+// 16-byte read of a source row of 64 bytes or more through the read-only path,
+// with the L2 told to fetch 64 bytes rather than a 128-byte line (half of
+// which would be another, randomly placed row)
 __device__ __forceinline__ int4 ld_row16_p64(const int4 *p) {
     int4 v;
     asm volatile("ld.global.nc.L2::64B.v4.s32 {%0,%1,%2,%3}, [%4];"
@@ -201,24 +202,26 @@ template <int NC>
 __global__ void __launch_bounds__(512)
     k_reorder_cols(const int32_t *__restrict__ perm, int32_t N, const int32_t *__restrict__ in, int32_t words,
                    ColList cols, int32_t ncols, int32_t *__restrict__ out) {
+    const bool wide = words >= 16;  // rows of 64 bytes or more: fetch 64 bytes per miss
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < N; r += int64_t(gridDim.x) * blockDim.x) {
         const int32_t src = perm ? __ldg(perm + r) : (int32_t)r;
         if ((uint32_t)src >= (uint32_t)N) continue;
         const int32_t *row = in + int64_t(src) * words;
+        auto rd = [wide](const int32_t *q) { return wide ? ld_row4_p64(q) : __ldg(q); };
         if (NC == 4) {
             int4 v;
-            v.x = __ldg(row + cols.c[0]);
-            v.y = __ldg(row + cols.c[1]);
-            v.z = __ldg(row + cols.c[2]);
-            v.w = __ldg(row + cols.c[3]);
+            v.x = rd(row + cols.c[0]);
+            v.y = rd(row + cols.c[1]);
+            v.z = rd(row + cols.c[2]);
+            v.w = rd(row + cols.c[3]);
             reinterpret_cast<int4 *>(out)[r] = v;
         } else if (NC == 2) {
             int2 v;
-            v.x = __ldg(row + cols.c[0]);
-            v.y = __ldg(row + cols.c[1]);
+            v.x = rd(row + cols.c[0]);
+            v.y = rd(row + cols.c[1]);
             reinterpret_cast<int2 *>(out)[r] = v;
         } else {
-            for (int c = 0; c < ncols; ++c) out[r * ncols + c] = __ldg(row + cols.c[c]);
+            for (int c = 0; c < ncols; ++c) out[r * ncols + c] = rd(row + cols.c[c]);
         }
     }
 }
@@ -230,14 +233,16 @@ __global__ void __launch_bounds__(512)
     k_reorder_query(const int32_t *__restrict__ perm, int32_t N, const int32_t *__restrict__ in, int32_t words,
                     int32_t fcol, int32_t flt, int32_t gcol, int32_t pcol, int32_t sentinel,
                     int2 *__restrict__ out) {
+    const bool wide = words >= 16;  // rows of 64 bytes or more: fetch 64 bytes per miss
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < N; r += int64_t(gridDim.x) * blockDim.x) {
         const int32_t src = perm ? __ldg(perm + r) : (int32_t)r;
         if ((uint32_t)src >= (uint32_t)N) continue;
         const int32_t *row = in + int64_t(src) * words;
-        const bool pass = fcol < 0 || __ldg(row + fcol) < flt;
+        auto rd = [wide](const int32_t *q) { return wide ? ld_row4_p64(q) : __ldg(q); };
+        const bool pass = fcol < 0 || rd(row + fcol) < flt;
         int2 v;
-        v.x = pass ? (gcol >= 0 ? __ldg(row + gcol) : 0) : sentinel;
-        v.y = pcol >= 0 ? __ldg(row + pcol) : 1;
+        v.x = pass ? (gcol >= 0 ? rd(row + gcol) : 0) : sentinel;
+        v.y = pcol >= 0 ? rd(row + pcol) : 1;
         out[r] = v;
     }
 }
@@ -329,8 +334,12 @@ cudaError_t launch_reorder(const int32_t *d_perm, int32_t N, const void *d_in, v
     if (N <= 0) return cudaSuccess;
     if (row_bytes % 16 == 0 && aligned16(d_in) && aligned16(d_out)) {
         const int32_t w = row_bytes / 16;
-        k_reorder16<<<grid_for(int64_t(N) * w, 512, 4), 512, 0, st>>>(d_perm, N, static_cast<const int4 *>(d_in),
-                                                                      static_cast<int4 *>(d_out), w);
+        if (row_bytes >= 64)  // wide rows: fetch 64 bytes per missed row, not a 128-byte line
+            k_reorder16<<<grid_for(int64_t(N) * w, 512, 4), 512, 0, st>>>(d_perm, N, static_cast<const int4 *>(d_in),
+                                                                          static_cast<int4 *>(d_out), w);
+        else
+            k_reorder<int4><<<grid_for(int64_t(N) * w, 512, 4), 512, 0, st>>>(
+                d_perm, N, static_cast<const int4 *>(d_in), static_cast<int4 *>(d_out), w);
     } else {
         const int32_t w = row_bytes / 4;
         k_reorder<int32_t><<<grid_for(int64_t(N) * w, 512, 4), 512, 0, st>>>(

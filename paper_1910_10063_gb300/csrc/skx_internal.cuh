@@ -120,6 +120,15 @@ __device__ __forceinline__ int ld_gather4(const int *p, uint64_t pol) {
     asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
+// A 4-byte read of a randomly placed row of 64 bytes or more, with the L2
+// prefetch-size hint .L2::64B: without it such a miss was seen to bring in a
+// whole 128-byte line, half of it another row.  (For narrow rows or small
+// arrays the longer line carries useful neighbours, and the hint was slower.)
+__device__ __forceinline__ int ld_row4_p64(const int *p) {
+    int v;
+    asm volatile("ld.global.nc.L2::64B.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
 
 __device__ __forceinline__ void raise_error(unsigned *err, unsigned bit) {
     if (err) atomicOr(err, bit);
