@@ -840,7 +840,7 @@ def run_serving(a, dev):
 
     result = {"table": f"{n // 1_000_000}M x {a.width * 4}B resident rows + resident rank (index from a 25N-row "
                        f"s=1.0 sample)", "pool_requests": len(pool), "pool_rows": pool_rows}
-    for mode, cfg in (("continuous_batching", skx.ServerConfig(max_inflight=64)),
+    for mode, cfg in (("continuous_batching", skx.ServerConfig()),  # library defaults: 128 in flight, 64M-row rounds
                       ("unbatched", skx.ServerConfig(max_inflight=1, round_rows=1 << 40))):
         srv = skx.Server(dim2, rank, cfg)
         run(srv, min(64, len(pool)), None)  # warm-up

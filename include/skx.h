@@ -437,9 +437,9 @@ skx_status skx_probe_batch(const void *d_rows, int32_t N, int32_t row_bytes, con
 typedef struct skx_server skx_server;
 
 typedef struct skx_server_config {
-    int32_t max_inflight;   /* requests admitted at once (device slots); default 64 */
+    int32_t max_inflight;   /* requests admitted at once (device slots); default 128 */
     int32_t tile_rows;      /* fact rows per batch tile; default 65536 */
-    int64_t round_rows;     /* fact rows per device round, over all requests; default 16 Mi */
+    int64_t round_rows;     /* fact rows per device round, over all requests; default 64 Mi */
     int64_t memory_budget;  /* device arena for admitted requests, bytes; default min(free/2, 16 GiB) */
     int32_t timeout_ms;     /* bound on any internal wait for the device; default 10000 */
     int32_t reserved0;

@@ -374,10 +374,10 @@ skx_status skx_server_create(const void *d_rows, int32_t N, int32_t row_bytes, c
     s->row_bytes = row_bytes;
     s->rank = d_rank;
     if (cfg) s->cfg = *cfg;
-    if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 64;
+    if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 128;
     if (s->cfg.tile_rows <= 0) s->cfg.tile_rows = 65536;
     s->cfg.tile_rows = (s->cfg.tile_rows + 3) & ~3;
-    if (s->cfg.round_rows <= 0) s->cfg.round_rows = int64_t(16) << 20;
+    if (s->cfg.round_rows <= 0) s->cfg.round_rows = int64_t(64) << 20;
     if (s->cfg.timeout_ms <= 0) s->cfg.timeout_ms = 10000;
     if (s->cfg.memory_budget <= 0) {
         size_t fr = 0, tot = 0;
