@@ -11,7 +11,7 @@
 //      matrix mat[b][cta] (plus one trailing zero);
 //   -  an exclusive scan of the matrix gives each CTA its write position in
 //      every bucket (and, at the end, the number of valid keys);
-//   C  each CTA re-reads its slice in tiles of 8192 keys, groups a tile by
+//   C  each CTA re-reads its slice in tiles of 16384 keys, groups a tile by
 //      bucket in shared memory, and writes the keys' 15-bit offsets in their
 //      bucket (2 bytes each) to its region of that bucket, so the part array
 //      holds every bucket's keys contiguously;
@@ -36,9 +36,9 @@ namespace {
 constexpr int kBktLog = 15;
 constexpr uint32_t kBkt = 1u << kBktLog;   // ids per bucket
 constexpr int kMaxBuckets = 8192;          // so N <= 2^28
-constexpr int kPBlock = 512;               // threads of phases A and C
-constexpr int kTileVec = 2048;             // 16-byte vectors per phase-C tile
-constexpr int kTileKeys = kTileVec * 4;    // 8192 keys
+constexpr int kPBlock = 1024;              // threads of phases A and C
+constexpr int kTileVec = 4096;             // 16-byte vectors per phase-C tile
+constexpr int kTileKeys = kTileVec * 4;    // 16384 keys
 constexpr int kVecPT = kTileVec / kPBlock; // vectors per thread per tile
 constexpr int kDBlock = 1024;              // threads of phase D
 constexpr int kDUnroll = 4;                // 16-byte vectors per thread per phase-D step
@@ -206,7 +206,7 @@ __host__ __device__ constexpr size_t scatter_smem_words(int B) {
 
 // Each tile is grouped by bucket in shared memory, then written in slot
 // order: consecutive threads write consecutive positions of one bucket's run.
-__global__ void __launch_bounds__(kPBlock, 2)
+__global__ void __launch_bounds__(kPBlock, 1)
     k_part_scatter(Slices s, const uint32_t *__restrict__ off, uint16_t *__restrict__ part, const uint32_t *run) {
     if (run && !*run) return;
     extern __shared__ uint32_t sm[];
@@ -510,11 +510,11 @@ struct PartLayout {
     size_t off_mat, off_bsum, off_queue, off_flag, off_part, total;
 };
 
-// CTAs of phases A and C: two per SM while phase C's shared memory allows it
+// CTAs of phases A and C: one 1024-thread CTA per SM (phase C holds 64
+// registers per thread, the whole register file)
 int part_grid(int32_t B) {
-    const size_t c = scatter_smem_words(B) * 4 + 33 * 4;
-    const int per_sm = c <= size_t(device_max_smem_optin()) / 2 - 1024 ? 2 : 1;
-    return device_sm_count() * per_sm;
+    (void)B;
+    return device_sm_count();
 }
 
 PartLayout part_layout(int32_t N, int64_t F) {
