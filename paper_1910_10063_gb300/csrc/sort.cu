@@ -10,7 +10,7 @@
 // sorted (8 bits per pass); descending order comes from sorting ~count.
 // Each pass is upsweep (per-tile digit counts) -> exclusive scan of the
 // digit-major count matrix -> downsweep (stable scatter).  Stability inside
-// a tile comes from processing each warp's 512 keys in 32-key rounds in
+// a tile comes from processing each warp's 128 keys in 32-key rounds in
 // order, ranking equal digits with __match_any_sync.  The final pass writes
 // perm[pos] = id and rank[id] = pos directly.
 //
@@ -31,11 +31,11 @@ namespace {
 
 constexpr int kBits = 8;
 constexpr int kBins = 1 << kBits;
-constexpr int kSortBlock = 256;            // 8 warps
+constexpr int kSortBlock = 1024;           // 32 warps
 constexpr int kWarps = kSortBlock / 32;
-constexpr int kRounds = 16;                // 32-key rounds per warp
+constexpr int kRounds = 4;                 // 32-key rounds per warp
 constexpr int kTile = kSortBlock * kRounds;  // 4096 keys per tile
-constexpr int kScanItems = 16;
+constexpr int kScanItems = 4;
 constexpr int kScanTile = kSortBlock * kScanItems;  // 4096
 
 __device__ __forceinline__ uint32_t first_key(const uint32_t *cnt, uint32_t i) { return ~cnt[i]; }
