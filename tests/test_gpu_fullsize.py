@@ -63,6 +63,28 @@ def test_large_build_remap_reorder_exact(large):
     idx.close()
 
 
+def test_partitioned_count_at_its_size_limit():
+    """The partitioned count at N = 2^28 ids (8192 buckets: the partition phase's shared memory
+    just under the per-block limit) and 2^28 + 3 keys, exact against the oracle; one id more and
+    the partitioned count is refused while the automatic count still answers (single pass)."""
+    n, f = 1 << 28, (1 << 28) + 3
+    w = synth.DeviceWorkload(n, f, 1.0, seed=14, width=1, device=DEV, with_measure=False, with_dim=False)
+    want = oracle.histogram(w.fk.cpu().numpy(), n)
+    c = skx.skx_count_ex(w.fk, n, skx.SKX_COUNT_PARTITIONED)
+    assert skx.skx_stream_status() == skx.SKX_OK
+    assert np.array_equal(c.cpu().numpy().view(np.uint32).astype(np.uint64), want)
+    del c
+    c = torch.empty(n + 1, dtype=torch.int32, device=DEV)
+    with pytest.raises(skx.SkxError) as e:
+        skx.skx_count_ex(w.fk, n + 1, skx.SKX_COUNT_PARTITIONED, counts=c)
+    assert e.value.status == skx.SKX_ENOTSUP
+    skx.skx_count(w.fk, n + 1, counts=c)
+    got = c.cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(got[:n], want) and got[n] == 0
+    del w, c
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("s", [0.0, 0.5, 1.0, 1.5])
 def test_large_probe_exact(large, s):
     w = large
