@@ -11,10 +11,12 @@
 //      matrix mat[b][cta] (plus one trailing zero);
 //   -  an exclusive scan of the matrix gives each CTA its write position in
 //      every bucket (and, at the end, the number of valid keys);
-//   C  each CTA re-reads its slice in tiles of 16384 keys, groups a tile by
-//      bucket in shared memory, and writes the keys' 15-bit offsets in their
-//      bucket (2 bytes each) to its region of that bucket, so the part array
-//      holds every bucket's keys contiguously;
+//   C  each CTA (1024 threads, one per SM) re-reads its slice in tiles of
+//      16384 keys (16 per thread), groups a tile by bucket in shared memory,
+//      and writes the keys' 15-bit offsets in their bucket (2 bytes each) to
+//      its region of that bucket, so the part array holds every bucket's keys
+//      contiguously; the longer a tile, the longer each bucket's run and the
+//      fewer partly written sectors;
 //   D  the buckets are cut into even chunks of at most 2^20 keys; a
 //      persistent grid takes chunks from an atomic counter and counts a chunk
 //      in 2^15 shared-memory counters, then writes them with plain stores (a
@@ -25,7 +27,8 @@
 // chunk (D), takes their most frequent bucket (offset) as its hot value, and
 // counts or ranks the keys equal to it in registers with one atomic per warp.
 // HBM traffic: the column twice (A, C), 2 bytes per key written (C) and read
-// (D), the counters written once.
+// (D), the counters written once.  Whether this count or the single pass
+// runs is decided on the device from a sample of the keys (k_count_choose).
 #include <algorithm>
 
 #include "skx_internal.cuh"
