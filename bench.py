@@ -355,6 +355,11 @@ def run_ours(a, rank, world, local_rank):
                 "algorithmic_bytes": {"count": "4F + 4N", "sort": "12N (read counts, write perm and rank)",
                                       "remap": "8F + 4N", "reorder": "2*row_bytes*N + 4N",
                                       "probe": f"8F + 16*D, D = expected distinct keys = {D:.4g}"}[dom]}
+    if roofline["traffic"]:
+        # the same launch measured on its actual DRAM bytes (ncu capture of this workload)
+        tgbs = roofline["traffic"] / (stage_avg[dom] * 1e-3) / 1e9
+        roofline["traffic_gbs"] = round(tgbs, 1)
+        roofline["traffic_frac"] = round(tgbs / peak, 4)
 
     # ---------------- plain vs remapped probe sweep over the skew
     sweep = []
