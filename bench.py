@@ -513,7 +513,9 @@ def run_ours(a, rank, world, local_rank):
         skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
         if not np.array_equal(h_out, result):
             raise RuntimeError("host-buffer path disagrees with the device-resident path")
-        n_e2e = max(3, min(a.steps, 5))
+        for _ in range(max(0, a.warmup - 1)):  # the checked call above is the first warm-up
+            skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
+        n_e2e = max(3, min(a.steps, 10))
         barrier()
         t = []
         for _ in range(n_e2e):

@@ -22,10 +22,13 @@
 //      in 2^15 shared-memory counters, then writes them with plain stores (a
 //      bucket in one chunk) or adds them with atomics (a bucket split over
 //      several chunks).
-// Same-address shared atomics serialise, and a bucket (or a chunk) can hold
-// a very hot id.  So each warp samples 32 keys of its tile (phases A, C) or
-// chunk (D), takes their most frequent bucket (offset) as its hot value, and
-// counts or ranks the keys equal to it in registers with one atomic per warp.
+// Same-address shared atomics serialise, and a bucket can hold most of a
+// tile when the column is very skewed.  So in phases A and C each warp
+// samples 32 keys of its tile, and when one bucket fills at least 12 of them
+// the warp counts or ranks that bucket's keys in registers with one atomic
+// per warp.  Phase D has no such path: its shared-memory adds return no
+// value, and measured over Zipf s = 0 .. 2 and an all-equal column the
+// plain adds were never slower than the register path.
 // HBM traffic: the column twice (A, C), 2 bytes per key written (C) and read
 // (D), the counters written once.  Whether this count or the single pass
 // runs is decided on the device from a sample of the keys (k_count_choose).
@@ -71,7 +74,7 @@ __device__ __forceinline__ int64_t extra_index(const Slices &s, int t) {
 
 // The most frequent of the warp's 32 values v (ties: the lowest lane's) in
 // the low 27 bits, its multiplicity (1..32) in the high 5 bits minus one.
-constexpr int kDominant = 4;  // a sampled value this frequent takes the register path
+constexpr int kDominant = 12;  // a sampled value this frequent takes the register path
 __device__ __forceinline__ uint32_t warp_mode(uint32_t v, uint32_t &mult) {
     const unsigned m = __match_any_sync(~0u, v);
     const uint32_t best = __reduce_max_sync(~0u, ((uint32_t)__popc(m) << 5) | (31u - lane_id()));
@@ -370,11 +373,6 @@ __global__ void __launch_bounds__(kDBlock, 1)
         const uint64_t b0 = off[size_t(b) * G];
         const uint64_t n = off[size_t(b + 1) * G] - b0;
         const uint64_t lo = b0 + n * j / nc, hi = b0 + n * (j + 1) / nc;
-        // the chunk's most frequent offset among 32 keys spread over it: if it
-        // is frequent there (a Zipf head id can hold most of a bucket), its
-        // keys are counted in registers (uniform branch for the block)
-        uint32_t mult;
-        const uint32_t hot = warp_mode(part[lo + ((hi - lo) * lane_id()) / 32], mult);
         uint64_t a0 = (lo + 7) & ~uint64_t(7);
         if (a0 > hi) a0 = hi;
         const uint64_t a1 = a0 + ((hi - a0) & ~uint64_t(7));
@@ -382,50 +380,23 @@ __global__ void __launch_bounds__(kDBlock, 1)
         for (uint64_t i = a1 + threadIdx.x; i < hi; i += kDBlock) atomicAdd(s_c + part[i], 1u);
         const int4 *p4 = reinterpret_cast<const int4 *>(part + a0);
         const uint64_t n4 = (a1 - a0) >> 3;
-        if (mult >= kDominant) {
-            uint32_t hc = 0;
-            for (uint64_t vb = threadIdx.x; vb < n4; vb += uint64_t(kDBlock) * kDUnroll) {
-                int4 x[kDUnroll];
-                bool ok[kDUnroll];
+        for (uint64_t vb = threadIdx.x; vb < n4; vb += uint64_t(kDBlock) * kDUnroll) {
+            int4 x[kDUnroll];
+            bool ok[kDUnroll];
 #pragma unroll
-                for (int u = 0; u < kDUnroll; ++u) {
-                    const uint64_t v = vb + uint64_t(u) * kDBlock;
-                    ok[u] = v < n4;
-                    x[u] = ok[u] ? ld_stream16(p4 + v, pol) : make_int4(0, 0, 0, 0);
-                }
-#pragma unroll
-                for (int u = 0; u < kDUnroll; ++u) {
-                    if (!ok[u]) continue;
-                    const uint32_t w[4] = {(uint32_t)x[u].x, (uint32_t)x[u].y, (uint32_t)x[u].z, (uint32_t)x[u].w};
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const uint32_t o = (w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;
-                        if (o == hot) ++hc;
-                        else atomicAdd(s_c + o, 1u);
-                    }
-                }
+            for (int u = 0; u < kDUnroll; ++u) {
+                const uint64_t v = vb + uint64_t(u) * kDBlock;
+                ok[u] = v < n4;
+                x[u] = ok[u] ? ld_stream16(p4 + v, pol) : make_int4(0, 0, 0, 0);
             }
-            hc = __reduce_add_sync(~0u, hc);
-            if (lane_id() == 0) atomicAdd(s_c + hot, hc);
-        } else {
-            for (uint64_t vb = threadIdx.x; vb < n4; vb += uint64_t(kDBlock) * kDUnroll) {
-                int4 x[kDUnroll];
-                bool ok[kDUnroll];
 #pragma unroll
-                for (int u = 0; u < kDUnroll; ++u) {
-                    const uint64_t v = vb + uint64_t(u) * kDBlock;
-                    ok[u] = v < n4;
-                    x[u] = ok[u] ? ld_stream16(p4 + v, pol) : make_int4(0, 0, 0, 0);
-                }
+            for (int u = 0; u < kDUnroll; ++u) {
+                if (!ok[u]) continue;
+                const uint32_t w[4] = {(uint32_t)x[u].x, (uint32_t)x[u].y, (uint32_t)x[u].z, (uint32_t)x[u].w};
 #pragma unroll
-                for (int u = 0; u < kDUnroll; ++u) {
-                    if (!ok[u]) continue;
-                    const uint32_t w[4] = {(uint32_t)x[u].x, (uint32_t)x[u].y, (uint32_t)x[u].z, (uint32_t)x[u].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        atomicAdd(s_c + (w[e] & 0xFFFFu), 1u);
-                        atomicAdd(s_c + (w[e] >> 16), 1u);
-                    }
+                for (int e = 0; e < 4; ++e) {
+                    atomicAdd(s_c + (w[e] & 0xFFFFu), 1u);
+                    atomicAdd(s_c + (w[e] >> 16), 1u);
                 }
             }
         }
