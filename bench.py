@@ -42,7 +42,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--mode", choices=["step", "cachefit"], default="step",
+    p.add_argument("--mode", choices=["step", "cachefit", "layouts"], default="step",
                    help="step: the timed path (default); cachefit: dimension-size sweep with 1B fact rows")
     p.add_argument("--n", type=int, default=20_000_000, help="dimension rows")
     p.add_argument("--f", type=int, default=500_000_000, help="fact rows")
@@ -51,6 +51,9 @@ def parse_args():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--sweep", default="0.0,0.5,1.0,1.5", help="Zipf exponents of the plain-vs-remapped probe sweep")
     p.add_argument("--sweep-steps", type=int, default=10)
+    p.add_argument("--ns", default="", help="dimension sizes of --mode layouts (default: --n)")
+    p.add_argument("--model-l2", default="", help="cache sizes in bytes at which --mode layouts evaluates "
+                   "the cache model (default: the device's L2)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--count-method", choices=["auto", "single", "partitioned"], default="auto",
                    help="count algorithm of the timed step (skx_count_ex); the library's automatic choice by default")
@@ -526,7 +529,7 @@ def run_ours(a, rank, world, local_rank):
         e2e = {"value": round(world * a.f * n_e2e / e2e_s / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": int(h_dim.numel() * 4 + 2 * a.f * 4), "d2h_bytes_per_step": 8 * 1000,
                "ms_per_step": round(1e3 * e2e_s / n_e2e, 3), "steps": n_e2e,
-               "ms_each": [round(1e3 * x, 2) for x in t],
+               "ms_each": [round(1e3 * x, 2) for x in t], "ms_median": round(1e3 * statistics.median(t), 3),
                "api": "skx_join_aggregate_host (pinned host buffers; H2D, build, remap, reorder, probe, D2H)"}
 
     # ---------------- CPU baseline: the oracle on a bounded sample
@@ -943,6 +946,85 @@ def run_reference(a, rank, world):
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_layouts(a):
+    """Plain vs remapped probe at one fixed launch shape over dimension sizes (--ns) and skews
+    (--sweep), every launch cold (L2 flushed before it), beside the Section III-C model's hit
+    rate for the gathers: 128-byte lines (a missing 16-byte gather was measured to bring in a
+    whole line), one LRU cache of each size in --model-l2.  No hot prefix, so both layouts run
+    the same kernel and differ only in where the rows lie.  Each
+    point issues W + K plain launches, then W + K remapped ones, in the order of `points`:
+    under ncu with -k regex:k_probe the captured launches follow that order."""
+    import torch
+    import paper_1910_10063_gb300 as skx
+    from paper_1910_10063_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    q = skx.Query.groupby_sum()
+    L2 = torch.cuda.get_device_properties(0).L2_cache_size
+    tuning = skx.Tuning()
+    for kv in (a.tuning or "block_threads=256,ctas_per_sm=8,unroll=1").split(","):
+        k, v = kv.split("=")
+        setattr(tuning, k.strip(), int(v))
+    tuning.hot_keys = -1
+    tuning.lane_keys = -1
+    ns = [int(x) for x in a.ns.split(",")] if a.ns else [a.n]
+    ss = [float(x) for x in a.sweep.split(",") if x.strip()] or [a.s]
+    row_b = a.width * 4
+    caps = [int(x) for x in a.model_l2.split(",")] if a.model_l2 else [int(L2)]
+
+    def launches(rows, keys, measure):
+        o = torch.empty(1000, dtype=torch.int64, device=dev)
+        ms = []
+        for i in range(a.warmup + a.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            skx.skx_probe_aggregate(rows, keys, measure, q, out=o, tuning=tuning)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= a.warmup:
+                ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms), o.cpu().numpy()
+
+    def model(p_row, line_bytes, cache_bytes):
+        rpl = max(1, line_bytes // row_b)
+        nl = (p_row.size + rpl - 1) // rpl
+        pad = np.zeros(nl * rpl)
+        pad[:p_row.size] = p_row
+        return round(skx.skx_cache_hit_rate(pad.reshape(nl, rpl).sum(axis=1), cache_bytes // line_bytes), 4)
+
+    points = []
+    for n in ns:
+        for s_ in ss:
+            w = synth.DeviceWorkload(n, a.f, s_, seed=a.seed, width=a.width, device=dev)
+            fk2 = torch.empty_like(w.fk)
+            dim2 = torch.empty_like(w.dim)
+            idx = skx.skx_build_index(w.fk, n)
+            skx.skx_remap(idx, w.fk, fk2)
+            skx.skx_reorder(idx, w.dim, dim2)
+            idx.close()
+            t_plain, r_plain = launches(w.dim, w.fk, w.measure)
+            t_rem, r_rem = launches(dim2, fk2, w.measure)
+            p_rank = np.diff(np.concatenate([[0.0], synth.zipf_cdf(n, s_)]))
+            rank_of_id = np.empty(n, dtype=np.int64)
+            rank_of_id[w.r2id_host] = np.arange(n)
+            p_id = p_rank[rank_of_id]
+            points.append({"N": n, "zipf_s": s_, "identical": bool(np.array_equal(r_plain, r_rem)),
+                           "plain_ms": round(t_plain, 4), "remapped_ms": round(t_rem, 4),
+                           "model_hit": {str(c): {"plain": model(p_id, 128, c), "remapped": model(p_rank, 128, c)}
+                                         for c in caps}})
+            del w, fk2, dim2
+            torch.cuda.empty_cache()
+    return {"mode": "layouts", "F": a.f, "row_bytes": row_b, "l2_bytes": int(L2), "model_line_bytes": 128,
+            "model_cache_bytes": caps, "warmup": a.warmup,
+            "steps": a.steps, "tuning": {k: tuning.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
+                                                                          "hot_keys", "lane_keys")},
+            "model": "Section III-C stack-distance model, one LRU cache", "status": skx.skx_stream_status(),
+            "points": points}
+
+
 def main():
     a = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -956,6 +1038,8 @@ def main():
         line = run_reference(a, rank, world)
     elif a.mode == "cachefit":
         line = run_cachefit(a) if rank == 0 else None
+    elif a.mode == "layouts":
+        line = run_layouts(a) if rank == 0 else None
     else:
         line = run_ours(a, rank, world, local_rank)
     if line is not None:
