@@ -127,6 +127,10 @@ def ncu_traffic(kernel_key, a=None):
 
 
 COUNT_METHODS = {"auto": 0, "single": 1, "partitioned": 2}
+# L2 bytes that a probe's dimension lines get on a GB300 while the fact columns stream past:
+# uniform keys (s = 0) miss with probability 1 - S/L under LRU, and their measured DRAM line
+# fetches give S = 82-91 MB at N = 2M..20M (profiles/probe_layouts_dram_N1M-20M_500M.txt).
+EFFECTIVE_L2_BYTES = 88_000_000
 
 
 def count_kernels(fk, n, f, method="auto"):
@@ -601,12 +605,23 @@ def predict_l2(a, w, line_bytes=128, tuning=None):
     p_fit /= p_fit.sum()
     lines_fit = lines(p_fit)
     hit_fit = skx.skx_cache_hit_rate(lines_fit, S)
+    S_eff = EFFECTIVE_L2_BYTES // line_bytes
+    hit_r_eff = skx.skx_cache_hit_rate(lines_r, S_eff)
+    hit_p_eff = skx.skx_cache_hit_rate(lines(p_rank[rank_of_id]), S_eff)
+    # the remapped probe's hit rate implied by its committed DRAM traffic: every miss brings in
+    # one line, and the fact columns add 8 bytes per row
+    traffic = ncu_traffic("k_probe", a)
+    hit_meas = None if traffic is None else round(1 - (traffic - 8 * a.f) / line_bytes / a.f, 4)
     t_l2 = skx.skx_cache_threshold(lines_r, S, 0.5, rows_per_line)
     t_l1 = skx.skx_cache_threshold(lines_r, S_l1, 0.5, rows_per_line)
     t_l2_fit = skx.skx_cache_threshold(lines_fit, S, 0.5, rows_per_line)
     return {"model": "Section III-C stack-distance model, LRU of the whole L2", "l2_bytes": int(L2),
             "line_bytes": line_bytes, "lines_in_cache": int(S), "dimension_lines": int(nl),
             "predicted_hit_remapped": round(hit_r, 4), "predicted_hit_plain": round(hit_p, 4),
+            "effective_l2_bytes": EFFECTIVE_L2_BYTES,
+            "predicted_hit_remapped_effective_l2": round(hit_r_eff, 4),
+            "predicted_hit_plain_effective_l2": round(hit_p_eff, 4),
+            "measured_hit_remapped_from_dram": hit_meas,
             "powerlaw_fit": {"points": int(ranks.size), "slope": round(slope, 4), "intercept": round(icpt, 3),
                              "zipf_s": a.s, "predicted_hit_remapped_from_fit": round(hit_fit, 4)},
             "threshold_t": {"rule": "ids whose line is a hit with probability >= 0.5 (Section IV-B)",
