@@ -910,14 +910,21 @@ def cpu_baseline(a, fk_host, m_host, dim_host, nthreads=None):
     dim2 = oracle.reorder(perm, dim_host)
     t["reorder"] = time.perf_counter() - t1
     t1 = time.perf_counter()
-    oracle.probe(dim2, fk2, m_host, nthreads=nthreads)
+    out_r = oracle.probe(dim2, fk2, m_host, nthreads=nthreads)
     t["probe"] = time.perf_counter() - t1
     total = time.perf_counter() - t0
+    # the same probe on the plain layout (outside the whole-path time): the oracle's own
+    # remapped-vs-plain ratio on the host cores
+    t1 = time.perf_counter()
+    out_p = oracle.probe(dim_host, fk_host, m_host, nthreads=nthreads)
+    t["probe_plain"] = time.perf_counter() - t1
     rows = fk_host.shape[0]
     return {"value": round(rows / total / 1e9, 5), "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"first {rows} of the {a.f} fact rows with the full {dim_host.shape[0]}-row dimension table; "
                       f"whole path (count, qsort, invert, remap, reorder single-threaded; probe on {nthreads} threads)",
-            "seconds": {k: round(v, 3) for k, v in t.items()}}
+            "seconds": {k: round(v, 3) for k, v in t.items()},
+            "probe_speedup_remapped_vs_plain": round(t["probe_plain"] / t["probe"], 3),
+            "probe_results_identical": bool(np.array_equal(np.asarray(out_r), np.asarray(out_p)))}
 
 
 # ====================================================================== reference
