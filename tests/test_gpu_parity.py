@@ -137,7 +137,10 @@ def test_count_auto_choice_parity(s):
 def test_count_methods_skewed_layouts(method):
     """Hot ids packed into bucket 0 (same-address shared atomics in every
     phase), one id holding every key (one bucket split into several chunks),
-    and ids that leave most buckets empty."""
+    ids that leave most buckets empty, and columns where about 40 % of the
+    keys fall in one bucket (or on one id) at random positions, so that a
+    warp's 32 sampled keys land on both sides of the register-path threshold
+    within one launch."""
     rng = np.random.default_rng(23)
     n = 1_000_000
     cdf = synth.zipf_cdf(n, 1.0)
@@ -145,7 +148,11 @@ def test_count_methods_skewed_layouts(method):
     fk_ident = synth.zipf_fk_host(cdf, ident, 5, 0, 4_000_003)
     fk_one = np.full(3_000_005, 777_777, dtype=np.int32)
     fk_sparse = rng.integers(0, 1000, 2_000_000).astype(np.int32) * 997
-    for fk in (fk_ident, fk_one, fk_sparse):
+    m = 3_000_017
+    in_b0 = rng.random(m) < 0.4
+    fk_mixed = np.where(in_b0, rng.integers(0, 32768, m), rng.integers(32768, n, m)).astype(np.int32)
+    fk_mixed_one = np.where(in_b0, 12_345, rng.integers(0, n, m)).astype(np.int32)
+    for fk in (fk_ident, fk_one, fk_sparse, fk_mixed, fk_mixed_one):
         c = skx.skx_count_ex(dev(fk), n, method)
         assert status() == skx.SKX_OK
         assert np.array_equal(_counts_np(c), oracle.histogram(fk, n))
