@@ -115,12 +115,14 @@ skx_status skx_build_index_from_counts(const uint32_t *d_counts, int32_t N, int6
  * The count of skx_count with the algorithm chosen by the caller (both give
  * identical counts; the choice only moves time between kernels):
  *   SKX_COUNT_AUTO         what skx_count and skx_build_index use.  For
- *                          2^24 <= N <= 2^28 and F >= 2^28 (when the
+ *                          2^16 <= N <= 2^28 and F >= 2^26 (when the
  *                          partitioned count's scratch can be allocated) a
  *                          kernel samples 8192 keys of d_fk and picks on the
  *                          device, without a host synchronisation: the single
- *                          pass when most sampled keys repeat in the sample
- *                          (heavy skew), else the partitioned count.  Smaller
+ *                          pass when 60 % or more of the sampled keys repeat
+ *                          in the sample (heavy skew), the partitioned count
+ *                          when fewer than 25 % do, and in between the
+ *                          partitioned count from N >= 2^22 ids.  Smaller
  *                          inputs take the single pass;
  *   SKX_COUNT_SINGLE_PASS  one pass over d_fk, a per-CTA shared-memory cache
  *                          of hot ids and L2 atomics for the rest;

@@ -130,7 +130,7 @@ cudaError_t launch_count(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_
     if (e != cudaSuccess || F <= 0) return e;
     bool part = method == SKX_COUNT_PARTITIONED;
     if (method == SKX_COUNT_AUTO)
-        part = N >= (1 << 24) && F >= (int64_t(1) << 28) && histogram_partitioned_fits(N, F);
+        part = N >= (1 << 16) && F >= (int64_t(1) << 26) && histogram_partitioned_fits(N, F);
     if (!part) return launch_histogram(d_fk, F, N, d_cnt, d_err, st);
     const size_t sb = histogram_partitioned_scratch(N, F);
     void *scratch = nullptr;

@@ -424,7 +424,14 @@ __global__ void __launch_bounds__(kDBlock, 1)
 constexpr int kSample = 8192;
 constexpr int kSampleLog = 14;
 constexpr int kSampleSlots = 1 << kSampleLog;  // open-addressing table, load <= 1/2
+// The choice, from the share of sampled keys whose id repeats in the sample
+// (about the share of the column the single pass's per-CTA cache absorbs):
+// at least kHotPerMille -> the single pass; below kFlatPerMille -> the
+// partitioned count; in between the partitioned count only from kMidSkewMinN
+// ids, below which the single pass's counters stay in L2 and it is as fast.
 constexpr uint32_t kHotPerMille = 600;
+constexpr uint32_t kFlatPerMille = 250;
+constexpr int32_t kMidSkewMinN = 1 << 22;
 constexpr int kChooseBlock = 1024;
 
 __global__ void __launch_bounds__(kChooseBlock)
@@ -474,8 +481,12 @@ __global__ void __launch_bounds__(kChooseBlock)
     dup = __reduce_add_sync(~0u, dup);
     if (lane_id() == 0) atomicAdd(&s_dup, dup);
     __syncthreads();
-    if (threadIdx.x == 0)
-        *flag = (s_valid > 0 && uint64_t(s_dup) * 1000 >= uint64_t(s_valid) * kHotPerMille) ? 0u : 1u;
+    if (threadIdx.x == 0) {
+        const uint64_t d = uint64_t(s_dup) * 1000, v = s_valid;
+        const bool heavy = v > 0 && d >= v * kHotPerMille;
+        const bool flat = v == 0 || d < v * kFlatPerMille;
+        *flag = heavy ? 0u : ((flat || N >= kMidSkewMinN) ? 1u : 0u);
+    }
 }
 
 struct PartLayout {

@@ -107,7 +107,7 @@ def _counts_np(c):
     (8, 10, 0.0, 1, 3),               # tiny: head and tail only, no full vector in most CTAs
     (32768, 100_001, 1.0, 2, 1),      # exactly one bucket of 2^15 ids
     (100_003, 3_000_001, 1.0, 3, 2),  # 4 buckets, the last ragged; many phase-C tiles
-    (2_500_000, 6_000_007, 1.0, 4, 0),  # the size-based choice takes the partitioned count
+    (2_500_000, 6_000_007, 1.0, 4, 0),  # 77 buckets, a few million keys
     (300_000, 4_000_000, 0.0, 5, 1),  # uniform
     (70_000, 5_000_000, 1.5, 6, 0),   # heavy skew: hot ids' buckets span several 2^20-key chunks
 ])
@@ -119,11 +119,17 @@ def test_count_methods_parity(method, n, f, s, seed, offset):
     assert np.array_equal(_counts_np(c), oracle.histogram(fk, n))
 
 
-@pytest.mark.parametrize("s", [1.0, 1.5])
-def test_count_auto_choice_parity(s):
+@pytest.mark.parametrize("n,f,s", [
+    (1 << 24, (1 << 28) + 5, 1.0),        # mid skew, many ids: partitioned
+    (1 << 24, (1 << 28) + 5, 1.5),        # heavy skew: the single pass
+    (1 << 16, (1 << 26) + 3, 0.0),        # the fewest sampled ids, flat: partitioned (2 buckets)
+    ((1 << 20) + 7, (1 << 26) + 3, 0.0),  # flat: partitioned
+    ((1 << 20) + 7, (1 << 26) + 3, 1.0),  # mid skew below 2^22 ids: the single pass
+    ((1 << 22) + 1, (1 << 26) + 9, 1.0),  # mid skew from 2^22 ids: partitioned
+])
+def test_count_auto_choice_parity(n, f, s):
     """Sizes where the automatic count samples the column and picks an
-    algorithm on the device (s = 1.5: the single pass; s = 1.0: partitioned)."""
-    n, f = 1 << 24, (1 << 28) + 5
+    algorithm on the device; every branch of the choice gives exact counts."""
     w = synth.DeviceWorkload(n, f, s, seed=12, width=1, device=DEV, with_measure=False, with_dim=False)
     expect = oracle.histogram(w.fk.cpu().numpy(), n)
     c = skx.skx_count(w.fk, n)
