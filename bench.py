@@ -132,6 +132,11 @@ COUNT_METHODS = {"auto": 0, "single": 1, "partitioned": 2}
 # uniform keys (s = 0) miss with probability 1 - S/L under LRU, and their measured DRAM line
 # fetches give S = 82-91 MB at N = 2M..20M (profiles/probe_layouts_dram_N1M-20M_500M.txt).
 EFFECTIVE_L2_BYTES = 88_000_000
+# Random 128-byte DRAM line fetches per second that the probe reaches on a 20M x 64 B table
+# (uniform keys, where nearly every gather misses: 464M fetches in 11.2 ms, less the 4 GB of
+# fact columns at the HBM peak; profiles/probe_layouts_dram_N1M-20M_500M.txt).  Smaller tables
+# reach more (49 G/s at 8M rows, 56 G/s at 4M: fewer DRAM pages and TLB entries in play).
+FETCH_RATE_20Mx64B = 44.0e9
 
 
 def count_kernels(fk, n, f, method="auto"):
@@ -368,6 +373,17 @@ def run_ours(a, rank, world, local_rank):
         tgbs = roofline["traffic"] / (stage_avg[dom] * 1e-3) / 1e9
         roofline["traffic_gbs"] = round(tgbs, 1)
         roofline["traffic_frac"] = round(tgbs / peak, 4)
+        if dom == "probe" and a.width * 4 == 64 and a.n == 20_000_000:
+            # what bounds this probe: random 128-byte line fetches (their rate, not their
+            # bytes), beside the fact columns' stream at the HBM peak
+            stream = 8 * a.f
+            fetches = (roofline["traffic"] - stream) / 128
+            floor_ms = 1e3 * (fetches / FETCH_RATE_20Mx64B + stream / (peak * 1e9))
+            roofline["line_fetch_bound"] = {
+                "line_fetches": int(fetches), "ceiling_per_s": FETCH_RATE_20Mx64B,
+                "floor_ms": round(floor_ms, 3), "frac": round(floor_ms / stage_avg[dom], 4),
+                "ceiling_source": "uniform keys over this 20M x 64 B table: 464M line fetches in 11.2 ms "
+                                  "less the fact stream (profiles/probe_layouts_dram_N1M-20M_500M.txt)"}
 
     # ---------------- plain vs remapped probe sweep over the skew
     sweep = []
