@@ -376,9 +376,9 @@ def run_ours(a, rank, world, local_rank):
         if dom == "probe" and a.width * 4 == 64 and a.n == 20_000_000:
             # what bounds this probe: random 128-byte line fetches (their rate, not their
             # bytes), beside the fact columns' stream at the HBM peak
-            stream = 8 * a.f
-            fetches = (roofline["traffic"] - stream) / 128
-            floor_ms = 1e3 * (fetches / FETCH_RATE_20Mx64B + stream / (peak * 1e9))
+            fact_bytes = 8 * a.f
+            fetches = (roofline["traffic"] - fact_bytes) / 128
+            floor_ms = 1e3 * (fetches / FETCH_RATE_20Mx64B + fact_bytes / (peak * 1e9))
             roofline["line_fetch_bound"] = {
                 "line_fetches": int(fetches), "ceiling_per_s": FETCH_RATE_20Mx64B,
                 "floor_ms": round(floor_ms, 3), "frac": round(floor_ms / stage_avg[dom], 4),
