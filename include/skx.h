@@ -68,7 +68,10 @@ uint64_t skx_kernel_launches(void);
  * Synchronises `stream`, then reports and clears the per-device data-error
  * word of the current device: SKX_EKEYRANGE or SKX_EGROUPRANGE if any kernel
  * of this library on this device met such data since the last call (from any
- * stream), SKX_ECUDA if the stream itself failed, else SKX_OK.
+ * stream), SKX_ETIMEOUT if a bounded device-side wait expired, SKX_EINVAL if
+ * a frequency sort met counts whose sum exceeds the F it was given,
+ * SKX_ECUDA if the stream itself failed, else SKX_OK.  The word is a fixed
+ * variable of the library's device image (no allocation).
  */
 skx_status skx_stream_status(void *stream);
 
@@ -104,8 +107,9 @@ skx_status skx_build_index(const int32_t *d_fk, int64_t F, int32_t N, void *stre
  * skx_count: d_counts[v] = #{i : d_fk[i] == v} for v in [0, N) (uint32,
  * fully overwritten; keys outside [0, N) are skipped and raise SKX_EKEYRANGE).
  * skx_build_index_from_counts: sorts the ids by (count desc, id asc) and
- * returns an index that takes a copy of the counts.  F is only an upper
- * bound on every count (it sets how many key bits are sorted).
+ * returns an index that takes a copy of the counts.  F bounds the sum of the
+ * counts (the fact rows they were taken from; it sets how many key bits are
+ * sorted); counts that break the bound give SKX_EINVAL at skx_stream_status.
  */
 skx_status skx_count(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_counts, void *stream);
 skx_status skx_build_index_from_counts(const uint32_t *d_counts, int32_t N, int64_t F, void *stream,
@@ -155,15 +159,25 @@ skx_status skx_count_ex(const int32_t *d_fk, int64_t F, int32_t N, uint32_t *d_c
  *
  * Same result as skx_build_index_from_counts: d_perm[r] (new -> old) and
  * d_rank[v] (old -> new), int32[N] in caller-owned device buffers, from
- * d_counts (uint32[N]); F bounds every count.  The scratch space is a fixed
- * ~16 MiB array inside the library's device image (held by every GPU that
- * loads the library until the process exits), so N is limited to
+ * d_counts (uint32[N]); F bounds the sum of the counts (counts that break
+ * the bound -- one above F, or more ids with a count of 255 or more than
+ * F / 255 allows -- are reported as SKX_EINVAL by skx_stream_status, and the
+ * order is then incomplete).  The scratch space is a
+ * fixed ~16 MiB array inside the library's device image, so N is limited to
  * skx_sort_by_count_noalloc_max_n() = 2^20 ids; a larger N is rejected
- * with SKX_EINVAL before anything is enqueued.  The first call on each device
- * looks up the array's device address (a CUDA runtime call, no allocation),
- * so make that first call before any stream capture.  All calls share the
- * one array: calls whose work overlaps on the GPU (different streams, or
- * different threads) race and must be serialised by the caller.
+ * with SKX_EINVAL before anything is enqueued.
+ *
+ * When the array is reserved: CUDA loads a library's device code lazily
+ * (unless CUDA_MODULE_LOADING=EAGER, which reserves the array when the
+ * library is loaded), so a device reserves the ~16 MiB the first time this
+ * function runs on it, and keeps it until the process exits.  A caller whose
+ * memory will later be tight should make that first call early: a call with
+ * N = 0 (the pointers may be NULL) does only this set-up and enqueues
+ * nothing.  Make it before any stream capture too.  Every later call looks
+ * up the array's device address again (no allocation; a cached address would
+ * go stale after cudaDeviceReset).  All calls share the one array: calls
+ * whose work overlaps on the GPU (different streams, or different threads)
+ * race and must be serialised by the caller.
  */
 skx_status skx_sort_by_count_noalloc(const uint32_t *d_counts, int32_t N, int64_t F, int32_t *d_perm,
                                      int32_t *d_rank, void *stream);

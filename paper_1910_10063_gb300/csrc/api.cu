@@ -23,12 +23,15 @@ struct skx_index {
     int32_t *rank;
 };
 
+// Per-device data-error word (bits kErr*): a fixed 4-byte variable of this
+// library's device image, so that no entry point has to allocate for it.
+static __device__ unsigned g_err_word_dev = 0;
+
 namespace skx {
 namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned *g_err_word[kMaxDevices] = {};
 int g_sms[kMaxDevices] = {};
 int g_smem_optin[kMaxDevices] = {};
 thread_local char g_last_cuda[256] = "no CUDA error";
@@ -104,17 +107,15 @@ skx_status cuda_status(cudaError_t e) {
     return SKX_ECUDA;
 }
 
+// The device address of the error word, looked up on every call with the
+// caller's device current.  Not cached: after cudaDeviceReset (or any
+// teardown of the primary context) a cached address would no longer be
+// mapped, and a kernel given it would fault.  The word is zero when the
+// module is loaded and is cleared by skx_stream_status.
 unsigned *device_error_word() {
-    const int d = current_device();
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_err_word[d]) {
-        unsigned *w = nullptr;
-        if (cudaMalloc(&w, sizeof(unsigned)) != cudaSuccess) return nullptr;
-        cudaMemset(w, 0, sizeof(unsigned));
-        cudaDeviceSynchronize();
-        g_err_word[d] = w;
-    }
-    return g_err_word[d];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_err_word_dev) != cudaSuccess) return nullptr;
+    return static_cast<unsigned *>(p);
 }
 
 int device_sm_count() {
@@ -174,7 +175,8 @@ skx_status make_index(int32_t N, int64_t F, cudaStream_t st, skx_index **out, Fi
     const size_t sb = sort_scratch_bytes(N, F);
     if (e == cudaSuccess && sb) e = cudaMallocAsync(&scratch, sb, st);
     if (e == cudaSuccess) e = fill(idx->counts);
-    if (e == cudaSuccess) e = launch_sort_by_count(idx->counts, N, F, idx->perm, idx->rank, scratch, sb, st);
+    if (e == cudaSuccess)
+        e = launch_sort_by_count(idx->counts, N, F, idx->perm, idx->rank, scratch, sb, device_error_word(), st);
     if (scratch) cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) {
         skx_status s = cuda_status(e);
@@ -222,6 +224,7 @@ skx_status skx_stream_status(void *stream) {
     if (h & kErrKeyRange) return SKX_EKEYRANGE;
     if (h & kErrGroupRange) return SKX_EGROUPRANGE;
     if (h & kErrTimeout) return SKX_ETIMEOUT;
+    if (h & kErrCountBound) return SKX_EINVAL;
     return SKX_OK;
 }
 

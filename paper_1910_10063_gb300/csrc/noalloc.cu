@@ -12,10 +12,11 @@
 // its own buffers.
 //
 // The array holds the scratch of the largest supported domain,
-// N <= kNoAllocMaxN ids (about 16 MiB); every GPU that loads the library
-// keeps it until the process exits.
-#include <mutex>
-
+// N <= kNoAllocMaxN ids (about 16 MiB).  A device reserves it when this
+// file's module is first loaded there -- the first call on that device, or
+// library load under CUDA_MODULE_LOADING=EAGER -- and keeps it until the
+// process exits.  A call with N = 0 does only that set-up, so a caller can
+// make it early, while memory is still free.
 #include "skx_internal.cuh"
 
 namespace skx {
@@ -28,24 +29,19 @@ constexpr size_t kNoAllocScratchBytes = sort_scratch_bound(size_t(kNoAllocMaxN))
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};  // device address of g_sort_scratch, per device
-
-// The array's name in host code is only a host-side stand-in; the device
-// address is looked up once per device, with that device current.
+// The array's name in host code is only a host-side stand-in; its device
+// address is looked up with the caller's device current, on every call.  The
+// address is not cached: after cudaDeviceReset (or any teardown of the
+// primary context) a cached one would no longer be mapped.  Once this file's
+// module is loaded on the device the lookup is cheap; the first lookup loads
+// it, and that is when the device reserves the array (CUDA loads modules
+// lazily unless CUDA_MODULE_LOADING=EAGER, which reserves it at library
+// load).
 skx_status scratch_address(void **out) {
-    int dev = 0;
-    SKX_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return SKX_ENOTSUP;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
-        if (e != cudaSuccess || p == nullptr) return cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess || p == nullptr) return cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+    *out = p;
     return SKX_OK;
 }
 
@@ -56,15 +52,19 @@ using namespace skx;
 
 extern "C" skx_status skx_sort_by_count_noalloc(const uint32_t *d_counts, int32_t N, int64_t F, int32_t *d_perm,
                                                 int32_t *d_rank, void *stream) {
-    if (N < 1 || F < 0 || F >= (int64_t(1) << 32) || !d_counts || !d_perm || !d_rank) return SKX_EINVAL;
+    if (N < 0 || F < 0 || F >= (int64_t(1) << 32)) return SKX_EINVAL;
     if (N > kNoAllocMaxN) return SKX_EINVAL;  // beyond the fixed scratch array
-    if (sort_scratch_bytes(N, F) > kNoAllocScratchBytes) return SKX_EINVAL;
     void *scratch = nullptr;
     skx_status s = scratch_address(&scratch);
     if (s != SKX_OK) return s;
+    unsigned *err = device_error_word();  // a __device__ variable as well: no allocation
+    if (!err) return SKX_ECUDA;
+    if (N == 0) return SKX_OK;  // set-up only: the array and the error word are now resident
+    if (!d_counts || !d_perm || !d_rank) return SKX_EINVAL;
+    if (sort_scratch_bytes(N, F) > kNoAllocScratchBytes) return SKX_EINVAL;
     // Nothing in the scratch needs to start at zero: every pass fully writes
     // the digit counts, block sums and key/id arrays before it reads them.
-    SKX_CUDA_TRY(launch_sort_by_count(d_counts, N, F, d_perm, d_rank, scratch, kNoAllocScratchBytes,
+    SKX_CUDA_TRY(launch_sort_by_count(d_counts, N, F, d_perm, d_rank, scratch, kNoAllocScratchBytes, err,
                                       static_cast<cudaStream_t>(stream)));
     return SKX_OK;
 }

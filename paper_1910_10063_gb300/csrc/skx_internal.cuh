@@ -12,12 +12,13 @@ namespace skx {
 constexpr unsigned kErrKeyRange = 1u;
 constexpr unsigned kErrGroupRange = 2u;
 constexpr unsigned kErrTimeout = 4u;
+constexpr unsigned kErrCountBound = 8u;  // a sort met a count above the bound F it was given
 
 constexpr int kWarp = 32;
 
 // -------------------------------------------------------------- host helpers
 skx_status cuda_status(cudaError_t e);          // records the message, maps to SKX_ECUDA
-unsigned *device_error_word();                  // per-device word (lazily allocated)
+unsigned *device_error_word();                  // the current device's word (a __device__ variable)
 int device_sm_count();                          // SMs of the current device
 int device_max_smem_optin();                    // max dynamic smem per block (opt-in)
 void note_launches(int n);                      // adds to the process-wide kernel-launch counter
@@ -178,8 +179,11 @@ constexpr size_t sort_scratch_bound(size_t n) {
 }
 size_t sort_scratch_bytes(int32_t N, int64_t F);
 // Sorts ids by (cnt desc, id asc): writes perm (new->old) and rank (old->new).
+// F must bound the sum of the counts.  A count above F, or more ids with a
+// count >= 255 than F / 255 allows, raises kErrCountBound on d_err (when not
+// null): the order would otherwise be silently incomplete.
 cudaError_t launch_sort_by_count(const uint32_t *d_cnt, int32_t N, int64_t F, int32_t *d_perm, int32_t *d_rank,
-                                 void *d_scratch, size_t scratch_bytes, cudaStream_t st);
+                                 void *d_scratch, size_t scratch_bytes, unsigned *d_err, cudaStream_t st);
 
 // Exclusive prefix sum of d_data[L] in place (3 kernels); d_block_sums needs
 // exclusive_scan_block_sums(L) entries.  With run_if_set, the kernels return

@@ -1,7 +1,7 @@
-// sort.cu -- order the dimension ids by decreasing frequency (Section III:
-// the offset representation lists the values "in decreasing frequency
-// order"; Section III-A: the sort runs over the small dimension domain), and
-// derive the rank representation (rank[perm[r]] = r) in the same pass.
+// sort.cu -- order the dimension ids by decreasing frequency (Section III,
+// the offset representation; Section III-A: the sort runs over the small
+// dimension domain), and derive the rank representation (rank[perm[r]] = r)
+// in the same pass.
 //
 // GB300 design: a stable least-significant-digit radix sort whose key is the
 // count and whose payload is the id.  The ids enter in ascending order, so
@@ -79,10 +79,14 @@ template <int SRC>
 __global__ void __launch_bounds__(kSortBlock)
     k_radix_upsweep(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ keys_in,
                     const uint32_t *__restrict__ vals_in, uint32_t n_host, const uint32_t *__restrict__ n_dev,
-                    int shift, uint32_t *__restrict__ tile_hist, uint32_t num_tiles) {
+                    int shift, uint32_t *__restrict__ tile_hist, uint32_t num_tiles, uint32_t cmax,
+                    unsigned *err) {
     __shared__ uint32_t s_cnt[kWarps][kBins];
     const uint32_t n = n_dev ? *n_dev : n_host;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    // a length read from the device that exceeds the grid (more heavy ids than the
+    // bound F / 255 allows) would leave ids unsorted: report it
+    if (n_dev && blockIdx.x == 0 && threadIdx.x == 0 && n > gridDim.x * kTile) raise_error(err, kErrCountBound);
     for (int i = threadIdx.x; i < kWarps * kBins; i += kSortBlock) (&s_cnt[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = blockIdx.x;
@@ -90,6 +94,7 @@ __global__ void __launch_bounds__(kSortBlock)
     if (tile * kTile < n) {  // tiles past the end (heavy passes) publish zero counts
         // all of the warp's loads first, so their latencies overlap; then the ranking rounds
         uint32_t dig[kRounds];
+        bool over = false;
 #pragma unroll
         for (int r = 0; r < kRounds; ++r) {
             const uint32_t i = base + r * 32 + lane;
@@ -98,8 +103,12 @@ __global__ void __launch_bounds__(kSortBlock)
                 uint32_t key, val;
                 load_key<SRC>(cnt, keys_in, vals_in, i, key, val);
                 dig[r] = (key >> shift) & (kBins - 1);
+                // the first pass reads every count: one above the bound F would be
+                // truncated to the sorted key bits
+                if ((SRC == kSrcClamped || SRC == kSrcCounts) && cnt[i] > cmax) over = true;
             }
         }
+        if (over) raise_error(err, kErrCountBound);
 #pragma unroll
         for (int r = 0; r < kRounds; ++r) {
             const uint32_t d = dig[r];
@@ -285,11 +294,16 @@ __global__ void __launch_bounds__(kSortBlock)
     }
 }
 
-__global__ void k_identity_perm(int32_t *__restrict__ perm, int32_t *__restrict__ rank, int32_t N) {
+// F == 0: every count must be 0 and the order is the identity
+__global__ void k_identity_perm(const uint32_t *__restrict__ cnt, int32_t *__restrict__ perm,
+                                int32_t *__restrict__ rank, int32_t N, unsigned *err) {
+    bool over = false;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
         perm[i] = (int32_t)i;
         rank[i] = (int32_t)i;
+        over |= cnt[i] != 0;
     }
+    if (over) raise_error(err, kErrCountBound);
 }
 
 int key_bits(int64_t F) {
@@ -340,6 +354,8 @@ namespace {
 
 struct Bufs {
     uint32_t *ka, *va, *kb, *vb, *hist, *bsum, *nh;
+    uint32_t cmax;  // bound on every count (F)
+    unsigned *err;  // data-error word, or null
 };
 
 template <int SRC, int OUT>
@@ -347,7 +363,8 @@ cudaError_t radix_pass(const uint32_t *cnt, const uint32_t *kin, const uint32_t 
                        const uint32_t *n_dev, uint32_t n_all, uint32_t tiles, int shift, const Bufs &b,
                        uint32_t *kout, uint32_t *vout, uint32_t *perm, int32_t *rank, cudaStream_t st) {
     const uint32_t L = tiles * kBins;
-    k_radix_upsweep<SRC><<<tiles, kSortBlock, 0, st>>>(cnt, kin, vin, n_host, n_dev, shift, b.hist, tiles);
+    k_radix_upsweep<SRC><<<tiles, kSortBlock, 0, st>>>(cnt, kin, vin, n_host, n_dev, shift, b.hist, tiles, b.cmax,
+                                                       b.err);
     cudaError_t e = exclusive_scan(b.hist, L, b.bsum, st);
     if (e != cudaSuccess) return e;
     k_radix_downsweep<SRC, OUT><<<tiles, kSortBlock, 0, st>>>(cnt, kin, vin, n_host, n_dev, n_all, shift, b.hist,
@@ -397,12 +414,12 @@ cudaError_t lsd_sort(const uint32_t *cnt, const uint32_t *ids, uint32_t n_host, 
 }  // namespace
 
 cudaError_t launch_sort_by_count(const uint32_t *d_cnt, int32_t N, int64_t F, int32_t *d_perm, int32_t *d_rank,
-                                 void *d_scratch, size_t scratch_bytes, cudaStream_t st) {
+                                 void *d_scratch, size_t scratch_bytes, unsigned *d_err, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     const int bits = key_bits(F);
     if (bits == 0) {  // F == 0: every count is 0, the order is the identity
         const int sms = device_sm_count();
-        k_identity_perm<<<sms * 4, 256, 0, st>>>(d_perm, d_rank, N);
+        k_identity_perm<<<sms * 4, 256, 0, st>>>(d_cnt, d_perm, d_rank, N, d_err);
         note_launches(1);
         return cudaGetLastError();
     }
@@ -418,6 +435,8 @@ cudaError_t launch_sort_by_count(const uint32_t *d_cnt, int32_t N, int64_t F, in
     b.hist = reinterpret_cast<uint32_t *>(w + s.off_hist);
     b.bsum = reinterpret_cast<uint32_t *>(w + s.off_bsum);
     b.nh = reinterpret_cast<uint32_t *>(w + s.off_nh);
+    b.cmax = (uint32_t)F;
+    b.err = d_err;
     const uint32_t n = (uint32_t)N;
     uint32_t *perm = reinterpret_cast<uint32_t *>(d_perm);
 

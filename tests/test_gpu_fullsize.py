@@ -5,11 +5,13 @@ times (autotuned probe, whole-row reorder, batched plan, serving loop).
   reorder compared with the oracle element by element, and the probe result at
   Zipf s in {0, 0.5, 1.0, 1.5} on the remapped layout compared with the oracle
   on the original layout.
-* 200M x 64-byte rows, 1B-row FK column (the largest cache-fit size): properties
-  that hold at any size -- perm is a bijection with rank its inverse, counts
-  sum to F and are non-increasing along perm with ascending ids among equal
-  counts, sampled counts equal direct counts, COUNT equals the sum of the counts
-  of passing ids, and the plain and remapped probes agree.
+* 200M x 64-byte rows, 1B-row FK column (the largest cache-fit size): counts,
+  perm, rank, remap, reorder and COUNT / SUM / GROUP BY SUM compared with the
+  oracle element by element, with the size-free properties (bijection,
+  inverse, non-increasing counts, ascending ids among ties, layout invariance)
+  checked beside them.
+* The drift variant (64M rows, 1B FK rows, 10 % of the ranks re-shuffled): the
+  stale index's probe and the rebuilt index against the oracle.
 * 512 batched queries and 256 served requests against the resident index,
   each compared with the oracle.
 """
@@ -108,10 +110,18 @@ def test_large_probe_exact(large, s):
     assert skx.skx_stream_status() == skx.SKX_OK
 
 
-def test_cachefit_largest_properties():
-    n, f = 200_000_000, 1_000_000_000
-    w = synth.DeviceWorkload(n, f, 1.0, seed=2, width=16, device=DEV)
-    idx = skx.skx_build_index(w.fk, n)
+def _host_equal_chunked(dev_t, host_a, chunk=1 << 28):
+    """dev_t (device tensor) equals host_a (numpy), compared in slices of the first axis."""
+    n = dev_t.shape[0]
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        if not np.array_equal(dev_t[a:b].cpu().numpy(), host_a[a:b]):
+            return False
+    return True
+
+
+def _index_properties(idx, fk, n, f):
+    """Properties that hold at any size, checked on the device beside the exact comparison."""
     perm, rank = idx.perm, idx.rank
     cnt = idx.counts.view(torch.int32).to(torch.int64)
     ar = torch.arange(n, device=DEV, dtype=torch.int32)
@@ -122,22 +132,97 @@ def test_cachefit_largest_properties():
     assert bool((c_by_rank[1:] <= c_by_rank[:-1]).all())                    # decreasing frequency
     ties = c_by_rank[1:] == c_by_rank[:-1]
     assert bool((perm[1:][ties] > perm[:-1][ties]).all())                   # ascending ids among ties
-    for v in np.random.default_rng(0).integers(0, n, 6).tolist() + [int(perm[0]), int(perm[1000])]:
-        assert int((w.fk == v).sum()) == int(cnt[v])                        # sampled direct counts
+
+
+QUERIES = {"groupby_sum": (oracle.AGG_GROUPBY_SUM, 1000), "count": (oracle.AGG_COUNT, 1),
+           "sum": (oracle.AGG_SUM, 1)}
+
+
+def _query(name):
+    return {"groupby_sum": skx.Query.groupby_sum(), "count": skx.Query.count(), "sum": skx.Query.sum()}[name]
+
+
+def test_cachefit_largest_exact():
+    """The largest cache-fit point, 200M x 64-byte rows and 1B FK rows at Zipf s = 1.0, element by
+    element against the oracle: counts, perm, rank, the remapped column, the reordered table, and
+    COUNT / SUM / GROUP BY SUM on the remapped layout (autotuned, as the sweep times it) against the
+    oracle's join over the original layout."""
+    n, f = 200_000_000, 1_000_000_000
+    w = synth.DeviceWorkload(n, f, 1.0, seed=2, width=16, device=DEV)
+    idx = skx.skx_build_index(w.fk, n)
     fk2 = torch.empty_like(w.fk)
     skx.skx_remap(idx, w.fk, fk2)
     dim2 = torch.empty_like(w.dim)
     skx.skx_reorder(idx, w.dim, dim2)
-    for q in (skx.Query.groupby_sum(), skx.Query.count(), skx.Query.sum()):
-        a = skx.skx_probe_aggregate(w.dim, w.fk, w.measure, q, tuning=skx.Tuning.plain())
-        b = skx.skx_probe_aggregate(dim2, fk2, w.measure, q)
-        assert torch.equal(a, b)                                            # layout invariance
-    passing = w.dim[:, 1] < 50
-    count = skx.skx_probe_aggregate(dim2, fk2, w.measure, skx.Query.count())
-    assert int(count[0]) == int(cnt[passing].sum())                         # COUNT = sum of counts
     assert skx.skx_stream_status() == skx.SKX_OK
+    _index_properties(idx, w.fk, n, f)
+    got = {}
+    for name in QUERIES:
+        q = _query(name)
+        t, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True)
+        got[name] = skx.skx_probe_aggregate(dim2, fk2, w.measure, q, tuning=t).cpu().numpy()
+        plain = skx.skx_probe_aggregate(w.dim, w.fk, w.measure, q, tuning=skx.Tuning.plain()).cpu().numpy()
+        assert np.array_equal(plain, got[name])                             # layout invariance
+    assert skx.skx_stream_status() == skx.SKX_OK
+
+    fk_h = w.fk.cpu().numpy()
+    cnt, perm, rank = oracle.build_index(fk_h, n)
+    assert np.array_equal(idx.counts.cpu().numpy().view(np.uint32).astype(np.uint64), cnt)
+    assert np.array_equal(idx.perm.cpu().numpy(), perm)
+    assert np.array_equal(idx.rank.cpu().numpy(), rank)
+    del cnt
+    assert _host_equal_chunked(fk2, oracle.remap(rank, fk_h))
+    dim_h = w.dim.cpu().numpy()
+    assert _host_equal_chunked(dim2, oracle.reorder(perm, dim_h))
+    m_h = w.measure.cpu().numpy()
+    for name, (agg, g) in QUERIES.items():
+        want = oracle.probe(dim_h, fk_h, m_h, agg, 1, 50, 0, g, 2 if agg != oracle.AGG_COUNT else -1,
+                            nthreads=THREADS)
+        assert np.array_equal(got[name], want), name
     idx.close()
     del w, fk2, dim2
+    torch.cuda.empty_cache()
+
+
+def test_cachefit_drift_exact():
+    """The drift variant of the cache-fit sweep (64M x 64-byte rows, 1B FK rows; 10 % of the ranks
+    re-shuffled): the stale index's probe of the drifted column and the rebuilt index, both against
+    the oracle on the original keys."""
+    n, f = 64_000_000, 1_000_000_000
+    w = synth.DeviceWorkload(n, f, 1.0, seed=0, width=16, device=DEV)
+    idx = skx.skx_build_index(w.fk, n)
+    dim2 = torch.empty_like(w.dim)
+    skx.skx_reorder(idx, w.dim, dim2)
+    r2d = synth.drift_rank_to_id(w.r2id_host, 0, 0.1)
+    wd = synth.DeviceWorkload(n, f, 1.0, seed=1, width=16, device=DEV, r2id=r2d, with_measure=False,
+                              with_dim=False)
+    q = skx.Query.groupby_sum()
+    fks = torch.empty_like(wd.fk)
+    skx.skx_remap(idx, wd.fk, fks)  # recode through the stale index
+    t, _ = skx.skx_probe_autotune(dim2, fks, w.measure, q, remapped=True)
+    stale = skx.skx_probe_aggregate(dim2, fks, w.measure, q, tuning=t).cpu().numpy()
+    idx2 = skx.skx_build_index(wd.fk, n)
+    skx.skx_remap(idx2, wd.fk, fks)
+    dim3 = torch.empty_like(dim2)
+    skx.skx_reorder(idx2, w.dim, dim3)
+    fresh = skx.skx_probe_aggregate(dim3, fks, w.measure, q, tuning=t).cpu().numpy()
+    assert skx.skx_stream_status() == skx.SKX_OK
+    _index_properties(idx2, wd.fk, n, f)
+
+    fkd_h = wd.fk.cpu().numpy()
+    cnt, perm, rank = oracle.build_index(fkd_h, n)
+    assert np.array_equal(idx2.counts.cpu().numpy().view(np.uint32).astype(np.uint64), cnt)
+    assert np.array_equal(idx2.perm.cpu().numpy(), perm)
+    assert np.array_equal(idx2.rank.cpu().numpy(), rank)
+    dim_h = w.dim.cpu().numpy()
+    assert _host_equal_chunked(fks, oracle.remap(rank, fkd_h))
+    assert _host_equal_chunked(dim3, oracle.reorder(perm, dim_h))
+    want = oracle.probe(dim_h, fkd_h, w.measure.cpu().numpy(), nthreads=THREADS)
+    assert np.array_equal(stale, want)
+    assert np.array_equal(fresh, want)
+    idx.close()
+    idx2.close()
+    del w, wd, fks, dim2, dim3
     torch.cuda.empty_cache()
 
 
