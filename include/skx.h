@@ -304,7 +304,17 @@ typedef struct skx_tuning {
     int32_t unroll;        /* 16-byte fact vectors per thread per step: 1 (default), 2 or 4 */
     int32_t gather_policy; /* L2 eviction priority of the dimension gathers: 1 evict_last,
                               2 evict_normal, 3 evict_first, 4 evict_unchanged (default 2) */
-    int32_t reserved[9];
+    int32_t split_keys;    /* t of the split (Section IV-B, remapped layout): fact rows with key
+                              >= t (the likely misses) are deferred to a second pass that
+                              resolves them bucket by bucket in rank order; keys in
+                              [hot_keys, t) are gathered at once.  Default (0) and -1: off.
+                              skx_split_threshold derives t from the index with the cache model.
+                              Needs t > hot_keys and fk, measure at the same offset mod 16 bytes
+                              (otherwise the probe runs unsplit); uses stream-ordered scratch of
+                              about 4 F bytes (deferred rows beyond F/2 are resolved at once). */
+    int32_t split_bucket;  /* log2 of the ranks per bucket of the second pass (default 19, range
+                              12..26; raised until there are at most 1024 buckets) */
+    int32_t reserved[7];
 } skx_tuning;
 
 skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,

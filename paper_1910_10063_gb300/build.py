@@ -26,7 +26,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 LIBS = {
     "libskx.so": {
         "dir": os.path.join(PKG, "csrc"),
-        "sources": ["api.cu", "histogram.cu", "histogram_part.cu", "sort.cu", "remap.cu", "probe.cu", "autotune.cu", "batch.cu", "server.cu", "operators.cu",
+        "sources": ["api.cu", "histogram.cu", "histogram_part.cu", "sort.cu", "remap.cu", "probe.cu", "probe_split.cu", "autotune.cu", "batch.cu", "server.cu", "operators.cu",
                     "cache_model.cu", "noalloc.cu"],
         "headers": ["skx_internal.cuh", "probe_core.cuh", os.path.join(INCLUDE, "skx.h")],
     },

@@ -216,6 +216,8 @@ skx_status validate_query(const skx_query *q, int32_t row_bytes) {
     return SKX_OK;
 }
 
+void resolve_hot(const ProbeArgs &a, skx_tuning &t, int64_t other_smem);
+
 // Fills the defaults of `t` in place.  Idempotent: a resolved tuning resolves
 // to itself ("off" and "as many as fit" are -1, never 0).
 void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t) {
@@ -226,6 +228,18 @@ void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t) {
     if (t.ctas_per_sm == 0) t.ctas_per_sm = 1024 / t.block_threads;
     if (t.ctas_per_sm < 0) t.ctas_per_sm = -1;
     if (t.gather_policy < 1 || t.gather_policy > 4) t.gather_policy = 2;
+    if (t.split_bucket < 12 || t.split_bucket > 26) t.split_bucket = 19;
+    if (t.split_keys <= 0 || t.split_keys >= a.N) t.split_keys = -1;
+    resolve_hot(a, t, t.split_keys > 0 ? kSplitSmemBytes : 0);
+    // the split needs keys [hot_keys, split_keys) to exist
+    const int32_t hot = t.hot_keys > 0 ? t.hot_keys : 0;
+    if (t.split_keys <= hot || t.split_keys >= a.N) t.split_keys = -1;
+    if (t.split_keys > 0) split_buckets(a.N, t.split_keys, &t.split_bucket);
+}
+
+// The hot prefix's shared-memory share: whatever the groups and, for the split
+// probe, its staging area (other_smem bytes) leave.
+void resolve_hot(const ProbeArgs &a, skx_tuning &t, int64_t other_smem) {
     if (t.hot_keys < 0) {
         t.hot_keys = -1;
         t.lane_keys = -1;
@@ -237,10 +251,10 @@ void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t) {
     if (t.lane_keys == 0) t.lane_keys = 32;
     if (t.lane_keys < 0) t.lane_keys = 0;
     if (t.hot_keys == 0) {  // sized so that two CTAs fit per SM
-        const int64_t budget = optin / 2 - 2048;
+        const int64_t budget = optin / 2 - 2048 - other_smem;
         t.hot_keys = (int32_t)(((budget - gbytes - int64_t(t.lane_keys) * 256) / 8) & ~int64_t(1023));
     }
-    const int64_t room = (optin - 1024 - gbytes) / 8;  // 8 bytes per hot key, 256 per lane-copied key
+    const int64_t room = (optin - 1024 - gbytes - other_smem) / 8;  // 8 bytes per hot key, 256 per lane key
     t.hot_keys = clamp32(t.hot_keys, 1, a.N);
     t.lane_keys = clamp32(t.lane_keys, 0, t.hot_keys);
     if (int64_t(t.hot_keys) + int64_t(t.lane_keys) * 32 > room) {
@@ -288,6 +302,11 @@ cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t s
     const size_t smem = size_t((gsmem ? a.q.num_groups : 0) + p.t_hot + p.t_lane * 32) * 8;
 
     const bool vec = af == am;
+    if (vec && t.split_keys > 0) {
+        bool ran = false;
+        e = launch_probe_split(p, a.q.agg, path, gsmem, t, st, &ran);
+        if (e != cudaSuccess || ran) return e;
+    }
     switch (a.q.agg) {
         case SKX_AGG_COUNT: return launch_agg<SKX_AGG_COUNT>(p, path, gsmem, t, smem, st, vec);
         case SKX_AGG_SUM: return launch_agg<SKX_AGG_SUM>(p, path, gsmem, t, smem, st, vec);

@@ -10,6 +10,9 @@ namespace skx {
 namespace pcore {
 
 constexpr int kMaxSmemGroups = 4096;
+// dynamic shared memory of the split probe's first pass beside groups and hot
+// prefix: 4096 staged rows of 10 bytes and two words per bucket (<= 1024)
+constexpr int64_t kSplitSmemBytes = 4096 * 10 + 1024 * 8;
 
 struct PP {
     const int32_t *fk, *measure;
@@ -142,4 +145,13 @@ __device__ __forceinline__ void handle(const PP &p, int32_t k, int32_t m, const 
 
 
 }  // namespace pcore
+
+// The probe with the split of Section IV-B (probe_split.cu): both passes
+// enqueued on st with their stream-ordered scratch.  *ran is false when the
+// tuning asks for no split or the scratch could not be allocated; nothing was
+// enqueued then and the caller runs the unsplit probe.  Needs the 16-byte
+// vector path (fk and measure at the same offset mod 16).
+cudaError_t launch_probe_split(const pcore::PP &p, int agg, int path, bool gsmem, const skx_tuning &t,
+                               cudaStream_t st, bool *ran);
+
 }  // namespace skx

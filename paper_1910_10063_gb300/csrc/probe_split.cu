@@ -1,0 +1,482 @@
+// probe_split.cu -- the FK-join probe with threshold-based splitting of the
+// fact stream (Section IV-B: ids below a threshold t are likely cache hits
+// and are resolved at once; the likely misses are written to a buffer and
+// resolved by a second pass over that buffer).
+//
+// On this GPU the cost of a miss is not its latency (resident warps hide
+// it) but the DRAM line it fetches: a cold dimension row that several fact
+// rows reference is evicted between its references by the streaming fact
+// columns and fetched again each time.  So the second pass here does more
+// than the paper's: the buffer is bucketed by rank range, and the pass walks
+// the buckets in rank order across the whole GPU, so that the dimension
+// lines of the bucket in progress stay in L2 and every cold line is fetched
+// close to once per probe.
+//
+// Pass 1 (k_probe_split), a persistent grid streaming fk and measure with
+// 16-byte loads, one vector per thread per sub-step:
+//   * k < t_hot          per-key shared-memory sums (threshold processing),
+//                        folded once per CTA at the end (as in probe.cu);
+//   * t_hot <= k < t     gathered and folded at once (likely L2 hits);
+//   * t <= k < N         deferred: staged in shared memory with its rank
+//                        within its bucket (bucket = (k - t) >> bshift).
+// After a sub-step that leaves at least kFlushAt rows staged, the CTA
+// reserves room for them in the global buffer (one atomic), lays them out
+// there bucket by bucket, and records each bucket's run in a bucket-major
+// run table (start[b][tau], count[b][tau], tau = the flush's number).  If
+// the buffer or the table is full, the CTA resolves its staged rows itself.
+// Pass 2 (k_probe_deferred): each warp takes units (bucket b, 8 consecutive
+// flushes) from an atomic counter in bucket-major order, concatenates the 8
+// runs, loads 128 entries at a time, gathers their rows and folds them.
+// Sums are exact modulo 2^64 in any order, so the result equals probe.cu's.
+#include <algorithm>
+
+#include "probe_core.cuh"
+
+namespace skx {
+namespace {
+
+using namespace pcore;
+
+constexpr int kSplitThreads = 512;
+constexpr int kStage = 4096;                          // staged rows per CTA
+constexpr int kFlushAt = kStage - 4 * kSplitThreads;  // one more sub-step always fits
+constexpr int kMaxBuckets = 1024;
+constexpr int kRunsPerUnit = 8;
+constexpr int kUnitBatch = 4;  // entries per lane per round of pass 2
+
+static_assert(kFlushAt > 0 && kStage <= 65536, "staging sizes");
+static_assert(int64_t(kStage) * 10 + int64_t(kMaxBuckets) * 8 <= kSplitSmemBytes, "staging smem budget");
+
+struct SP {
+    int2 *miss;        // deferred (key, measure) rows, cap entries
+    uint32_t cap;
+    uint32_t *tstart;  // [B][max_tiles]
+    uint32_t *tcnt;    // [B][max_tiles]
+    uint32_t max_tiles;
+    uint32_t *ctr;     // [0] rows reserved, [1] flushes numbered, [2] pass-2 units taken
+    int32_t t_split;
+    int32_t bshift;
+    int32_t B;
+};
+
+__device__ __forceinline__ void st_evict_first8(int2 *p, int2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.s32 [%0], {%1,%2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ int2 ld_stream8(const int2 *p, uint64_t pol) {
+    int2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s32 {%0,%1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, unsigned lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= (unsigned)o) v += y;
+    }
+    return v;
+}
+
+struct Stage {
+    int2 *rows;       // kStage entries
+    uint16_t *rank;   // kStage ranks within their bucket
+    uint32_t *cnt;    // B
+    uint32_t *off;    // B
+    uint32_t *fill;   // 1
+    uint32_t *misc;   // base, tau, ok
+};
+
+// Moves the staged rows to the global buffer (or resolves them here when it is
+// full) and clears the stage.  Called by every thread of the CTA, after a
+// barrier, with the same stage contents.
+template <int AGG, int PATH, bool GSMEM>
+__device__ void flush_stage(const PP &p, const SP &d, const Stage &s, uint64_t pol_g, uint64_t pol_w,
+                            unsigned long long &acc, unsigned long long *s_grp) {
+    const uint32_t n = *s.fill;
+    const unsigned lane = lane_id();
+    if (threadIdx.x < 32) {
+        uint32_t carry = 0;
+        for (int b0 = 0; b0 < d.B; b0 += 32) {
+            const int b = b0 + (int)lane;
+            const uint32_t c = b < d.B ? s.cnt[b] : 0u;
+            const uint32_t incl = warp_incl_scan(c, lane);
+            if (b < d.B) s.off[b] = carry + incl - c;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) {
+            const uint32_t base = atomicAdd(d.ctr + 0, n);
+            const uint32_t tau = atomicAdd(d.ctr + 1, 1u);
+            s.misc[0] = base;
+            s.misc[1] = tau;
+            s.misc[2] = (uint64_t(base) + n <= uint64_t(d.cap) && tau < d.max_tiles) ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    const uint32_t base = s.misc[0], tau = s.misc[1];
+    const bool ok = s.misc[2] != 0;
+    if (tau < d.max_tiles)
+        for (int b = threadIdx.x; b < d.B; b += blockDim.x) {
+            const size_t ti = size_t(b) * d.max_tiles + tau;
+            d.tstart[ti] = base + s.off[b];
+            d.tcnt[ti] = ok ? s.cnt[b] : 0u;
+        }
+    if (ok) {
+        for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+            const int2 v = s.rows[e];
+            const int b = (v.x - d.t_split) >> d.bshift;
+            st_evict_first8(d.miss + (size_t(base) + s.off[b] + s.rank[e]), v, pol_w);
+        }
+    } else {
+        // no room left: resolve the staged rows here
+        for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+            const int2 v = s.rows[e];
+            const int4 row = fetch_row<PATH, AGG>(p, v.x, pol_g);
+            const unsigned long long amount = AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)v.y;
+            fold<AGG, GSMEM>(p, row, amount, acc, s_grp);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < d.B; b += blockDim.x) s.cnt[b] = 0;
+    if (threadIdx.x == 0) *s.fill = 0;
+    __syncthreads();
+}
+
+template <int AGG, int PATH, bool GSMEM>
+__global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
+    extern __shared__ unsigned long long smem[];
+    __shared__ uint32_t s_fill, s_misc[4];
+    const int ngrp = GSMEM ? p.G : 0;
+    unsigned long long *s_grp = smem;
+    HotArrays h;
+    h.lo = reinterpret_cast<uint32_t *>(smem + ngrp);
+    h.hi = reinterpret_cast<int32_t *>(h.lo + p.t_hot);
+    h.lane_lo = reinterpret_cast<uint32_t *>(h.hi + p.t_hot);
+    h.lane_hi = reinterpret_cast<int32_t *>(h.lane_lo + (p.t_lane << 5));
+    const int nsm = ngrp + p.t_hot + (p.t_lane << 5);  // 8-byte words
+    Stage s;
+    s.rows = reinterpret_cast<int2 *>(smem + nsm);
+    s.rank = reinterpret_cast<uint16_t *>(s.rows + kStage);
+    s.cnt = reinterpret_cast<uint32_t *>(s.rank + kStage);
+    s.off = s.cnt + d.B;
+    s.fill = &s_fill;
+    s.misc = s_misc;
+    for (int i = threadIdx.x; i < nsm; i += blockDim.x) smem[i] = 0;
+    for (int b = threadIdx.x; b < d.B; b += blockDim.x) s.cnt[b] = 0;
+    if (threadIdx.x == 0) s_fill = 0;
+    __syncthreads();
+
+    const uint64_t pol_s = policy_evict_first();
+    const uint64_t pol_g = policy_by_code(p.gather_policy);
+    const unsigned lane = lane_id();
+    unsigned long long acc = 0;
+    const uint32_t t_hot = (uint32_t)p.t_hot, t_split = (uint32_t)d.t_split, nkeys = (uint32_t)p.N;
+
+    const int4 *fk4 = reinterpret_cast<const int4 *>(p.fk + p.head);
+    const int4 *m4 = reinterpret_cast<const int4 *>((AGG == SKX_AGG_COUNT ? p.fk : p.measure) + p.head);
+    const int64_t nvec = (p.F - p.head) >> 2;
+    const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+    const int64_t cta0 = int64_t(blockIdx.x) * blockDim.x;
+
+    int4 nk = make_int4(0, 0, 0, 0), nm = make_int4(0, 0, 0, 0);
+    if (cta0 + threadIdx.x < nvec) {
+        nk = ld_stream16(fk4 + cta0 + threadIdx.x, pol_s);
+        if (AGG != SKX_AGG_COUNT) nm = ld_stream16(m4 + cta0 + threadIdx.x, pol_s);
+    }
+    // every thread of the CTA runs the same number of sub-steps (base is CTA-uniform)
+    for (int64_t base = cta0; base < nvec; base += nthr) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < nvec;
+        const int32_t key[4] = {nk.x, nk.y, nk.z, nk.w};
+        const int32_t mea[4] = {nm.x, nm.y, nm.z, nm.w};
+        int4 row[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t k = (uint32_t)key[j];
+            row[j] = make_int4(0, 0, 0, 0);
+            if (valid && k >= t_hot && k < t_split) row[j] = fetch_row<PATH, AGG>(p, key[j], pol_g);
+        }
+        if (i + nthr < nvec) {
+            nk = ld_stream16(fk4 + i + nthr, pol_s);
+            if (AGG != SKX_AGG_COUNT) nm = ld_stream16(m4 + i + nthr, pol_s);
+        }
+        uint32_t ndef = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t k = (uint32_t)key[j];
+            if (!valid) continue;
+            if (k < t_hot) {
+                if (k < (uint32_t)p.t_lane) {
+                    const size_t li = (size_t(k) << 5) + lane;
+                    hot_add<AGG>(HotRef{h.lane_lo + li, h.lane_hi + li}, mea[j]);
+                } else {
+                    hot_add<AGG>(HotRef{h.lo + k, h.hi + k}, mea[j]);
+                }
+            } else if (k >= t_split) {
+                if (k < nkeys) ++ndef;
+                else raise_error(p.err, kErrKeyRange);
+            }
+        }
+        // stage slots for the warp's deferred rows: one shared atomic per warp
+        const uint32_t incl = warp_incl_scan(ndef, lane);
+        const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t wbase = 0;
+        if (lane == 31 && wtot) wbase = atomicAdd(&s_fill, wtot);
+        uint32_t slot = __shfl_sync(0xffffffffu, wbase, 31) + incl - ndef;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t k = (uint32_t)key[j];
+            if (valid && k >= t_split && k < nkeys) {
+                const uint32_t b = (k - t_split) >> d.bshift;
+                const uint32_t r = atomicAdd(s.cnt + b, 1u);
+                s.rows[slot] = make_int2(key[j], mea[j]);
+                s.rank[slot] = (uint16_t)r;
+                ++slot;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t k = (uint32_t)key[j];
+            if (valid && k >= t_hot && k < t_split) {
+                const unsigned long long amount = AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)mea[j];
+                fold<AGG, GSMEM>(p, row[j], amount, acc, s_grp);
+            }
+        }
+        __syncthreads();
+        if (s_fill >= (uint32_t)kFlushAt) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, s_grp);
+    }
+    __syncthreads();
+    if (s_fill > 0) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, s_grp);
+
+    // unaligned head (< 4 rows) and ragged tail (< 4 rows): resolved here
+    const int64_t tid = cta0 + threadIdx.x;
+    if (tid < 8) {
+        const int64_t tail0 = p.head + (nvec << 2);
+        int64_t idx = -1;
+        if (tid < p.head) idx = tid;
+        else if (tid >= 4 && tail0 + (tid - 4) < p.F) idx = tail0 + (tid - 4);
+        if (idx >= 0) {
+            const int32_t k = p.fk[idx];
+            const int32_t m = AGG == SKX_AGG_COUNT ? 0 : p.measure[idx];
+            int4 r = make_int4(0, 0, 0, 0);
+            if ((uint32_t)k >= t_hot && (uint32_t)k < nkeys) r = fetch_row<PATH, AGG>(p, k, pol_g);
+            handle<AGG, PATH, GSMEM>(p, k, m, r, acc, s_grp, h, lane);
+        }
+    }
+    __syncthreads();
+
+    // hot prefix: one lookup per hot row per CTA
+    for (int k = threadIdx.x; k < p.t_hot; k += blockDim.x) {
+        unsigned long long sum = hot_value(h.lo[k], h.hi[k]);
+        if (k < p.t_lane) {
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l)
+                sum += hot_value(h.lane_lo[(size_t(k) << 5) + l], h.lane_hi[(size_t(k) << 5) + l]);
+        }
+        if (sum == 0) continue;
+        const int4 v = fetch_row<PATH, AGG>(p, k, pol_g);
+        fold<AGG, GSMEM>(p, v, sum, acc, s_grp);
+    }
+    if (AGG == SKX_AGG_GROUPBY_SUM) {
+        if (GSMEM) {
+            __syncthreads();
+            for (int g = threadIdx.x; g < p.G; g += blockDim.x)
+                if (s_grp[g]) atomicAdd(p.out + g, s_grp[g]);
+        }
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0 && acc) atomicAdd(p.out, acc);
+    }
+}
+
+// Pass 2: the deferred rows, bucket by bucket.
+template <int AGG, int PATH, bool GSMEM>
+__global__ void __launch_bounds__(kSplitThreads, 2) k_probe_deferred(PP p, SP d) {
+    extern __shared__ unsigned long long smem[];
+    const int ngrp = GSMEM ? p.G : 0;
+    unsigned long long *s_grp = smem;
+    for (int i = threadIdx.x; i < ngrp; i += blockDim.x) smem[i] = 0;
+    __syncthreads();
+    const uint64_t pol_s = policy_evict_first();
+    const uint64_t pol_g = policy_by_code(p.gather_policy);
+    const unsigned lane = lane_id();
+    unsigned long long acc = 0;
+    const uint32_t used = *(volatile uint32_t *)(d.ctr + 1);
+    const uint32_t n_tiles = used < d.max_tiles ? used : d.max_tiles;
+    const uint32_t upb = (n_tiles + kRunsPerUnit - 1) / kRunsPerUnit;  // units per bucket
+    const uint64_t total = uint64_t(upb) * uint64_t(d.B);
+    for (;;) {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(d.ctr + 2, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (uint64_t(u) >= total) break;
+        const uint32_t b = u / upb, tau0 = (u % upb) * kRunsPerUnit;
+        uint32_t c = 0, st = 0;
+        if (lane < (unsigned)kRunsPerUnit && tau0 + lane < n_tiles) {
+            const size_t ti = size_t(b) * d.max_tiles + tau0 + lane;
+            c = d.tcnt[ti];
+            st = d.tstart[ti];
+        }
+        const uint32_t incl = warp_incl_scan(c, lane);
+        const uint32_t excl = incl - c;
+        const uint32_t T = __shfl_sync(0xffffffffu, incl, kRunsPerUnit - 1);
+        for (uint32_t j0 = 0; j0 < T; j0 += 32 * kUnitBatch) {
+            int2 e[kUnitBatch];
+            bool v[kUnitBatch];
+#pragma unroll
+            for (int q = 0; q < kUnitBatch; ++q) {
+                const uint32_t j = j0 + q * 32 + lane;
+                // run of entry j: the number of runs whose inclusive end is <= j
+                uint32_t t = 0;
+                if (__shfl_sync(0xffffffffu, incl, 3) <= j) t = 4;
+                if (__shfl_sync(0xffffffffu, incl, t + 1) <= j) t += 2;
+                if (__shfl_sync(0xffffffffu, incl, t) <= j) t += 1;
+                const uint32_t rs = __shfl_sync(0xffffffffu, st, t);
+                const uint32_t rx = __shfl_sync(0xffffffffu, excl, t);
+                v[q] = j < T;
+                e[q] = make_int2(0, 0);
+                if (v[q]) e[q] = ld_stream8(d.miss + (size_t(rs) + (j - rx)), pol_s);
+            }
+            int4 row[kUnitBatch];
+#pragma unroll
+            for (int q = 0; q < kUnitBatch; ++q) {
+                row[q] = make_int4(0, 0, 0, 0);
+                if (v[q]) row[q] = fetch_row<PATH, AGG>(p, e[q].x, pol_g);
+            }
+#pragma unroll
+            for (int q = 0; q < kUnitBatch; ++q)
+                if (v[q]) {
+                    const unsigned long long amount =
+                        AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)e[q].y;
+                    fold<AGG, GSMEM>(p, row[q], amount, acc, s_grp);
+                }
+        }
+    }
+    if (AGG == SKX_AGG_GROUPBY_SUM) {
+        if (GSMEM) {
+            __syncthreads();
+            for (int g = threadIdx.x; g < p.G; g += blockDim.x)
+                if (s_grp[g]) atomicAdd(p.out + g, s_grp[g]);
+        }
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0 && acc) atomicAdd(p.out, acc);
+    }
+}
+
+template <typename K>
+cudaError_t persistent_grid(K kern, size_t smem, int ctas_per_sm, int64_t work_threads, int *grid) {
+    cudaError_t e = set_smem_limit_once(reinterpret_cast<const void *>(kern), -1);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSplitThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    int64_t g = int64_t(device_sm_count()) * per_sm;
+    const int64_t need = (work_threads + kSplitThreads - 1) / kSplitThreads;
+    if (need < g) g = need < 1 ? 1 : need;
+    *grid = (int)g;
+    return cudaSuccess;
+}
+
+// Sizes, allocates (stream-ordered), launches both passes and frees.  *ran is
+// false when the scratch could not be allocated (nothing was enqueued then).
+template <int AGG, int PATH, bool GSMEM>
+cudaError_t run_split(const PP &p, const skx_tuning &t, int32_t bshift, int32_t B, cudaStream_t st, bool *ran) {
+    *ran = false;
+    auto k1 = k_probe_split<AGG, PATH, GSMEM>;
+    auto k2 = k_probe_deferred<AGG, PATH, GSMEM>;
+    const size_t grp = size_t(GSMEM ? p.G : 0) * 8;
+    const size_t smem1 = grp + size_t(p.t_hot + p.t_lane * 32) * 8 + size_t(kStage) * 10 + size_t(B) * 8;
+    const int resident1 = t.ctas_per_sm > 0 ? std::max(1, t.ctas_per_sm * t.block_threads / kSplitThreads) : -1;
+    const int64_t nvec = (p.F - p.head) >> 2;
+    int g1 = 0, g2 = 0;
+    cudaError_t e = persistent_grid(k1, smem1, resident1, nvec, &g1);
+    if (e != cudaSuccess) return e;
+    e = persistent_grid(k2, grp, -1, int64_t(1) << 40, &g2);
+    if (e != cudaSuccess) return e;
+
+    SP d{};
+    d.t_split = t.split_keys;
+    d.bshift = bshift;
+    d.B = B;
+    // Deferred rows beyond half the column are resolved in pass 1 (if more
+    // than half the rows miss, splitting them off no longer pays).  Flush
+    // numbers: one per kFlushAt reserved rows, a last one per CTA, and up to
+    // one per CTA that raced a failed reservation.
+    const uint64_t cap = std::min<uint64_t>(uint64_t(p.F), uint64_t(p.F) / 2 + uint64_t(kStage) * g1);
+    d.cap = (uint32_t)cap;
+    d.max_tiles = (uint32_t)(cap / kFlushAt + 2 * uint64_t(g1) + 2);
+    const size_t table = size_t(B) * d.max_tiles * 4;
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t off_start = 256, off_cnt = off_start + up(table), off_miss = off_cnt + up(table);
+    const size_t bytes = off_miss + size_t(cap) * 8;
+    char *w = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&w), bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    d.ctr = reinterpret_cast<uint32_t *>(w);
+    d.tstart = reinterpret_cast<uint32_t *>(w + off_start);
+    d.tcnt = reinterpret_cast<uint32_t *>(w + off_cnt);
+    d.miss = reinterpret_cast<int2 *>(w + off_miss);
+    *ran = true;
+    e = cudaMemsetAsync(d.ctr, 0, 16, st);
+    if (e == cudaSuccess) {
+        k1<<<(unsigned)g1, kSplitThreads, smem1, st>>>(p, d);
+        k2<<<(unsigned)g2, kSplitThreads, grp, st>>>(p, d);
+        note_launches(2);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(w, st);
+    return e;
+}
+
+template <int AGG, int PATH>
+cudaError_t run_split_g(const PP &p, bool gsmem, const skx_tuning &t, int32_t bshift, int32_t B, cudaStream_t st,
+                        bool *ran) {
+    if (AGG == SKX_AGG_GROUPBY_SUM && gsmem) return run_split<AGG, PATH, true>(p, t, bshift, B, st, ran);
+    return run_split<AGG, PATH, false>(p, t, bshift, B, st, ran);
+}
+
+template <int AGG>
+cudaError_t run_split_p(const PP &p, int path, bool gsmem, const skx_tuning &t, int32_t bshift, int32_t B,
+                        cudaStream_t st, bool *ran) {
+    if (path == kRow16) return run_split_g<AGG, kRow16>(p, gsmem, t, bshift, B, st, ran);
+    if (path == kRow8) return run_split_g<AGG, kRow8>(p, gsmem, t, bshift, B, st, ran);
+    return run_split_g<AGG, kRowGeneric>(p, gsmem, t, bshift, B, st, ran);
+}
+
+}  // namespace
+
+int32_t split_buckets(int32_t N, int32_t t_split, int32_t *bshift) {
+    int32_t sh = *bshift;
+    int64_t b = ((int64_t(N) - t_split) + (int64_t(1) << sh) - 1) >> sh;
+    while (b > kMaxBuckets) {
+        ++sh;
+        b = ((int64_t(N) - t_split) + (int64_t(1) << sh) - 1) >> sh;
+    }
+    *bshift = sh;
+    return (int32_t)b;
+}
+
+cudaError_t launch_probe_split(const PP &p, int agg, int path, bool gsmem, const skx_tuning &t, cudaStream_t st,
+                               bool *ran) {
+    *ran = false;
+    if (t.split_keys <= 0 || t.split_keys >= p.N || t.split_keys < p.t_hot) return cudaSuccess;
+    int32_t bshift = t.split_bucket;
+    const int32_t B = split_buckets(p.N, t.split_keys, &bshift);
+    switch (agg) {
+        case SKX_AGG_COUNT: return run_split_p<SKX_AGG_COUNT>(p, path, gsmem, t, bshift, B, st, ran);
+        case SKX_AGG_SUM: return run_split_p<SKX_AGG_SUM>(p, path, gsmem, t, bshift, B, st, ran);
+        default: return run_split_p<SKX_AGG_GROUPBY_SUM>(p, path, gsmem, t, bshift, B, st, ran);
+    }
+}
+
+}  // namespace skx
