@@ -341,6 +341,16 @@ skx_status skx_probe_default_tuning(int32_t N, int32_t row_bytes, int64_t F, con
 skx_status skx_probe_autotune(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
                               const int32_t *d_measure, int64_t F, const skx_query *q, int remapped,
                               int64_t *d_out, void *stream, skx_tuning *out, float *best_ms);
+/* The same search, plus the split probe when remapped != 0 and hint is not
+ * NULL with hint->split_keys = t_model > 0 (for example from
+ * skx_split_threshold): split thresholds t_model / 2, t_model and 2 t_model,
+ * each with hot_keys in {off, 2048, 8192} and one or as many CTAs per SM as
+ * fit.  Other fields of hint are ignored.  skx_probe_autotune is this call
+ * with hint = NULL. */
+skx_status skx_probe_autotune_ex(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
+                                 const int32_t *d_measure, int64_t F, const skx_query *q, int remapped,
+                                 const skx_tuning *hint, int64_t *d_out, void *stream, skx_tuning *out,
+                                 float *best_ms);
 
 /* ------------------------------------------------------------------------
  * The paper's other operators over the remapped layout.
@@ -393,6 +403,21 @@ skx_status skx_cache_threshold(const double *h_f, int64_t L, int64_t S, double p
  * skipped).  Host only.  Errors: SKX_EINVAL (null pointer, fewer than two
  * usable points, all usable x equal). */
 skx_status skx_powerlaw_fit(const double *h_x, const double *h_y, int64_t n, double *slope, double *intercept);
+
+/* The threshold t of the split probe (skx_tuning.split_keys; Section IV-B)
+ * derived from an index with the Section III-C model, as the paper suggests:
+ * the index's counts at 48 log-spaced ranks (gathered on the device; `stream`
+ * is synchronised) are fitted to a power law (skx_powerlaw_fit), the fitted
+ * frequencies are summed over the 128-byte lines of a remapped table with
+ * rows of row_bytes, and *t = skx_cache_threshold(those lines, S =
+ * cache_bytes / 128, p, rows per line), capped at N.  cache_bytes = 0 takes
+ * two thirds of the device's L2 (the share the probe's dimension lines were
+ * measured to keep while the fact columns stream past).  Host work is
+ * O(N log N) (about a second at N = 20M).  Errors: SKX_EINVAL (null pointer,
+ * N < 2, bad row_bytes, p outside (0, 1], negative cache_bytes, fewer than
+ * two nonzero counts), SKX_ENOMEM, SKX_ECUDA. */
+skx_status skx_split_threshold(const skx_index *idx, int32_t row_bytes, int64_t cache_bytes, double p, int64_t *t,
+                               void *stream);
 
 /* Counts of chosen ranks of an index, the input of a frequency fit:
  * h_counts[k] = counts[perm[h_ranks[k]]] (the count of the id with

@@ -148,6 +148,12 @@ def lib():
             L.skx_probe_autotune.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), ctypes.c_int, P, P,
                                              ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_float)]
             L.skx_probe_autotune.restype = st
+            L.skx_probe_autotune_ex.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), ctypes.c_int,
+                                                ctypes.POINTER(Tuning), P, P, ctypes.POINTER(Tuning),
+                                                ctypes.POINTER(ctypes.c_float)]
+            L.skx_probe_autotune_ex.restype = st
+            L.skx_split_threshold.argtypes = [P, i32, i64, ctypes.c_double, ctypes.POINTER(i64), P]
+            L.skx_split_threshold.restype = st
             L.skx_batch_plan_create.argtypes = [P, i32, i32, ctypes.POINTER(ProbeDesc), i32, ctypes.POINTER(Tuning), i32,
                                                 P, ctypes.POINTER(P)]
             L.skx_batch_plan_create.restype = st
@@ -424,18 +430,35 @@ def skx_probe_default_tuning(n: int, row_bytes: int, f: int, query: Query, remap
     return t
 
 
-def skx_probe_autotune(rows, fk, measure, query: Query, remapped: bool = True, out=None, stream=None):
-    """Returns (Tuning, estimated ms for the full F) chosen by timing candidates on this data."""
+def skx_probe_autotune(rows, fk, measure, query: Query, remapped: bool = True, out=None, stream=None,
+                       split_hint: int = 0):
+    """Returns (Tuning, estimated ms for the full F) chosen by timing candidates on this data.
+    split_hint > 0 (a split threshold, e.g. from skx_split_threshold) adds the split probe's
+    candidates around it (skx_probe_autotune_ex)."""
     import torch
     if out is None:
         out = torch.empty(query.nout, dtype=torch.int64, device=fk.device)
     t = Tuning()
     ms = ctypes.c_float()
-    _check(lib().skx_probe_autotune(_dptr(rows, "rows"), rows.shape[0], _row_bytes(rows),
-                                    _dptr(fk, "fk", torch.int32), _dptr(measure, "measure", torch.int32),
-                                    fk.numel(), ctypes.byref(query), int(remapped), _dptr(out, "out", torch.int64),
-                                    _stream(stream), ctypes.byref(t), ctypes.byref(ms)), "skx_probe_autotune")
+    hint = None
+    if split_hint and split_hint > 0:
+        hint = Tuning()
+        hint.split_keys = int(split_hint)
+    _check(lib().skx_probe_autotune_ex(_dptr(rows, "rows"), rows.shape[0], _row_bytes(rows),
+                                       _dptr(fk, "fk", torch.int32), _dptr(measure, "measure", torch.int32),
+                                       fk.numel(), ctypes.byref(query), int(remapped),
+                                       ctypes.byref(hint) if hint is not None else None,
+                                       _dptr(out, "out", torch.int64), _stream(stream), ctypes.byref(t),
+                                       ctypes.byref(ms)), "skx_probe_autotune_ex")
     return t, ms.value
+
+
+def skx_split_threshold(index: "Index", row_bytes: int, cache_bytes: int = 0, p: float = 0.5, stream=None) -> int:
+    """The split threshold t (Section IV-B) from the index's counts through the Section III-C model."""
+    t = ctypes.c_int64()
+    _check(lib().skx_split_threshold(index._h, int(row_bytes), int(cache_bytes), float(p), ctypes.byref(t),
+                                     _stream(stream)), "skx_split_threshold")
+    return t.value
 
 
 def _descs(items):

@@ -1,5 +1,6 @@
-// autotune.cu -- picks the probe's launch shape and hot-prefix threshold by
-// timing candidates on the caller's own data, and caches the choice.
+// autotune.cu -- picks the probe's launch shape, hot-prefix threshold and
+// split threshold by timing candidates on the caller's own data, and caches
+// the choice.
 //
 // The threshold t of threshold-based processing (Section IV-B) depends on
 // the skew and on the cache sizes; the paper derives it from a cost model or
@@ -33,6 +34,26 @@ Key key_of(int32_t N, int32_t row_bytes, const skx_query &q, int64_t F, int rema
     int d = 0;
     cudaGetDevice(&d);
     return Key(d, N, row_bytes, q.agg, log2_bucket(F), remapped ? 1 : 0);
+}
+
+// Candidates of the split probe around the model's threshold t_model (Section
+// IV-B): half, equal and twice t, with and without a shared-memory hot prefix,
+// at the split kernels' 512 threads with one or as many CTAs per SM as fit.
+void split_candidates(int32_t N, int32_t t_model, std::vector<skx_tuning> &c) {
+    if (t_model <= 0) return;
+    for (int64_t tm : {int64_t(t_model) / 2, int64_t(t_model), int64_t(t_model) * 2})
+        for (int h : {-1, 2048, 8192})
+            for (int cps : {-1, 1}) {
+                if (tm <= (h > 0 ? h : 0) || tm >= N) continue;
+                skx_tuning t{};
+                t.block_threads = 512;
+                t.unroll = 1;
+                t.ctas_per_sm = cps;
+                t.hot_keys = h;
+                t.lane_keys = h == -1 ? -1 : 0;
+                t.split_keys = (int32_t)tm;
+                c.push_back(t);
+            }
 }
 
 std::vector<skx_tuning> candidates(int remapped, int32_t N) {
@@ -81,9 +102,10 @@ bool cached_probe_tuning(int32_t N, int32_t row_bytes, const skx_query &q, int64
 
 using namespace skx;
 
-extern "C" skx_status skx_probe_autotune(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
-                                         const int32_t *d_measure, int64_t F, const skx_query *q, int remapped,
-                                         int64_t *d_out, void *stream, skx_tuning *out, float *best_ms) {
+extern "C" skx_status skx_probe_autotune_ex(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
+                                            const int32_t *d_measure, int64_t F, const skx_query *q, int remapped,
+                                            const skx_tuning *hint, int64_t *d_out, void *stream, skx_tuning *out,
+                                            float *best_ms) {
     if (!out) return SKX_EINVAL;
     skx_status s = validate_query(q, row_bytes);
     if (s != SKX_OK) return s;
@@ -110,7 +132,9 @@ extern "C" skx_status skx_probe_autotune(const void *d_rows, int32_t N, int32_t 
     float best = 1e30f;
     skx_tuning best_t{};
     bool any = false;
-    for (skx_tuning t : candidates(remapped, N)) {
+    std::vector<skx_tuning> cand = candidates(remapped, N);
+    if (remapped && hint && hint->split_keys > 0) split_candidates(N, hint->split_keys, cand);
+    for (skx_tuning t : cand) {
         resolve_probe_tuning(a, t);
         float ms_min = 1e30f;
         bool ok = true;
@@ -140,4 +164,11 @@ extern "C" skx_status skx_probe_autotune(const void *d_rows, int32_t N, int32_t 
     *out = best_t;
     if (best_ms) *best_ms = best * float(F) / float(sample);
     return SKX_OK;
+}
+
+extern "C" skx_status skx_probe_autotune(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
+                                         const int32_t *d_measure, int64_t F, const skx_query *q, int remapped,
+                                         int64_t *d_out, void *stream, skx_tuning *out, float *best_ms) {
+    return skx_probe_autotune_ex(d_rows, N, row_bytes, d_fk, d_measure, F, q, remapped, nullptr, d_out, stream, out,
+                                 best_ms);
 }

@@ -163,4 +163,58 @@ skx_status skx_powerlaw_fit(const double *h_x, const double *h_y, int64_t n, dou
     return SKX_OK;
 }
 
+// The split threshold of Section IV-B from the index, the paper's way: sample
+// the value-frequency distribution (the index's counts at log-spaced ranks),
+// fit it to a power law (a line in a log-log plot), and run the cache model
+// on the fitted frequencies of the remapped table's lines.
+skx_status skx_split_threshold(const skx_index *idx, int32_t row_bytes, int64_t cache_bytes, double p, int64_t *t,
+                               void *stream) {
+    if (!idx || !t || row_bytes < 4 || row_bytes % 4 != 0 || cache_bytes < 0 || !(p > 0.0 && p <= 1.0))
+        return SKX_EINVAL;
+    const int32_t N = skx_index_size(idx);
+    if (N < 2) return SKX_EINVAL;
+    constexpr int64_t kLine = 128;
+    if (cache_bytes == 0) {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
+            l2 <= 0)
+            return SKX_ECUDA;
+        // the share of the L2 that a probe's dimension lines keep while the fact
+        // columns stream past (measured with uniform keys: about two thirds)
+        cache_bytes = int64_t(l2) * 2 / 3;
+    }
+    const int64_t S = std::max<int64_t>(1, cache_bytes / kLine);
+    std::vector<int64_t> ranks;
+    for (int k = 0; k < 48; ++k) {
+        const int64_t r = int64_t(std::floor(std::exp(std::log(double(N)) * k / 47.0))) - 1;
+        const int64_t rr = std::min<int64_t>(N - 1, std::max<int64_t>(0, r));
+        if (ranks.empty() || rr > ranks.back()) ranks.push_back(rr);
+    }
+    std::vector<uint32_t> cnt(ranks.size());
+    skx_status st = skx_index_counts_at_ranks(idx, ranks.data(), int64_t(ranks.size()), cnt.data(), stream);
+    if (st != SKX_OK) return st;
+    std::vector<double> x(ranks.size()), y(ranks.size());
+    for (size_t k = 0; k < ranks.size(); ++k) {
+        x[k] = double(ranks[k] + 1);
+        y[k] = double(cnt[k]);
+    }
+    double slope = 0.0, icpt = 0.0;
+    st = skx_powerlaw_fit(x.data(), y.data(), int64_t(x.size()), &slope, &icpt);
+    if (st != SKX_OK) return st;
+    const int32_t rows_per_line = std::max<int32_t>(1, int32_t(kLine / row_bytes));
+    const int64_t L = (int64_t(N) + rows_per_line - 1) / rows_per_line;
+    std::vector<double> f(L, 0.0);
+    double total = 0.0;
+    for (int64_t r = 0; r < N; ++r) {
+        const double w = std::pow(double(r + 1), slope);
+        f[r / rows_per_line] += w;
+        total += w;
+    }
+    if (!(total > 0.0)) return SKX_EINVAL;
+    for (double &v : f) v /= total;
+    st = skx_cache_threshold(f.data(), L, S, p, rows_per_line, t);
+    if (st == SKX_OK && *t > N) *t = N;
+    return st;
+}
+
 }  // extern "C"

@@ -245,8 +245,12 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
                 fold<AGG, GSMEM>(p, row[j], amount, acc, s_grp);
             }
         }
-        __syncthreads();
-        if (s_fill >= (uint32_t)kFlushAt) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, s_grp);
+        // The stage's fill after this sub-step is the largest value any warp's
+        // reservation returned, so the barrier's OR over those tells every thread
+        // the same answer (reading s_fill itself here would race with warps that
+        // already reserve for the next sub-step).
+        const bool full = lane == 31 && wtot && wbase + wtot >= (uint32_t)kFlushAt;
+        if (__syncthreads_or(full)) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, s_grp);
     }
     __syncthreads();
     if (s_fill > 0) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, s_grp);
