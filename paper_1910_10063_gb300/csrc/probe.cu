@@ -34,7 +34,9 @@ template <int AGG, int PATH, bool GSMEM, int UNROLL>
 __global__ void __launch_bounds__(512) k_probe(PP p) {
     extern __shared__ unsigned long long smem[];
     const int ngrp = GSMEM ? p.G : 0;
-    unsigned long long *s_grp = smem;
+    GrpRef g;
+    g.lo = reinterpret_cast<uint32_t *>(smem);
+    g.hi = g.lo + ngrp;
     HotArrays h;
     h.lo = reinterpret_cast<uint32_t *>(smem + ngrp);
     h.hi = reinterpret_cast<int32_t *>(h.lo + p.t_hot);
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
             }
 #pragma unroll
             for (int j = 0; j < 4 * U; ++j)
-                if (valid[j / 4]) handle<AGG, PATH, GSMEM>(p, key[j], mea[j], row[j], acc, s_grp, h, lane);
+                if (valid[j / 4]) handle_row<AGG, PATH, GSMEM>(p, key[j], mea[j], row[j], acc, g, h, lane);
         }
         // unaligned head (< 4 rows) and ragged tail (< 4 rows)
         if (tid < 8) {
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
                 int4 row = make_int4(0, 0, 0, 0);
                 if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N)
                     row = fetch_row<PATH, AGG>(p, k, pol_g);
-                handle<AGG, PATH, GSMEM>(p, k, m, row, acc, s_grp, h, lane);
+                handle_row<AGG, PATH, GSMEM>(p, k, m, row, acc, g, h, lane);
             }
         }
     } else {
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
             const int32_t m = AGG == SKX_AGG_COUNT ? 0 : ld_stream4(p.measure + i, pol_s);
             int4 row = make_int4(0, 0, 0, 0);
             if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N) row = fetch_row<PATH, AGG>(p, k, pol_g);
-            handle<AGG, PATH, GSMEM>(p, k, m, row, acc, s_grp, h, lane);
+            handle_row<AGG, PATH, GSMEM>(p, k, m, row, acc, g, h, lane);
         }
     }
     __syncthreads();
@@ -135,20 +137,9 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
         }
         if (s == 0) continue;
         const int4 v = fetch_row<PATH, AGG>(p, k, pol_g);
-        fold<AGG, GSMEM>(p, v, s, acc, s_grp);
+        fold_sum<AGG, GSMEM>(p, v, s, acc, g);
     }
-
-    if (AGG == SKX_AGG_GROUPBY_SUM) {
-        if (GSMEM) {
-            __syncthreads();
-            for (int g = threadIdx.x; g < p.G; g += blockDim.x)
-                if (s_grp[g]) atomicAdd(p.out + g, s_grp[g]);
-        }
-    } else {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0 && acc) atomicAdd(p.out, acc);
-    }
+    flush_groups<AGG, GSMEM>(p, acc, g);
 }
 
 template <int AGG, int PATH, bool GSMEM, int UNROLL>

@@ -120,10 +120,111 @@ __device__ __forceinline__ unsigned long long hot_value(uint32_t lo, int32_t hi)
     return (unsigned long long)lo + ((unsigned long long)(long long)hi << 32);
 }
 
+// Group sums of one CTA as two 32-bit shared words per group (32-bit shared
+// atomics are native; a 64-bit shared add is several times slower): lo takes
+// the low words of the 64-bit products, hi their high words plus one for each
+// carry out of lo, which the returning add on lo reveals exactly.  So
+// sum = lo + 2^32 * hi (mod 2^64), bit for bit.
+struct GrpRef {
+    uint32_t *lo, *hi;  // G each
+};
+
+__device__ __forceinline__ void add64_split(uint32_t *lo, uint32_t *hi, unsigned long long x) {
+    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
+    const uint32_t old = atomicAdd(lo, xl);
+    const uint32_t inc = xh + (old + xl < old ? 1u : 0u);
+    if (inc) atomicAdd(hi, inc);
+}
+
+// Fold of one fact row (measure m) whose gathered values are v: the product is
+// formed as one signed 32 x 32 -> 64 multiply.
+template <int AGG, bool GSMEM>
+__device__ __forceinline__ void fold_row(const PP &p, const int4 &v, int32_t m, unsigned long long &acc, GrpRef g) {
+    if (!passes(p, v)) return;
+    if (AGG == SKX_AGG_COUNT) {
+        acc += 1ull;
+        return;
+    }
+    const unsigned long long prod = (unsigned long long)((long long)m * (long long)v.z);
+    if (AGG == SKX_AGG_SUM) {
+        acc += prod;
+        return;
+    }
+    if ((uint32_t)v.y < (uint32_t)p.G) {
+        if (GSMEM)
+            add64_split(g.lo + v.y, g.hi + v.y, prod);
+        else
+            atomicAdd(p.out + v.y, prod);
+    } else {
+        raise_error(p.err, kErrGroupRange);
+    }
+}
+
+// Fold of a hot row's 64-bit measure sum (or count) s.
+template <int AGG, bool GSMEM>
+__device__ __forceinline__ void fold_sum(const PP &p, const int4 &v, unsigned long long s, unsigned long long &acc,
+                                         GrpRef g) {
+    if (!passes(p, v)) return;
+    if (AGG == SKX_AGG_COUNT) {
+        acc += s;
+        return;
+    }
+    const unsigned long long prod = s * (unsigned long long)(long long)v.z;
+    if (AGG == SKX_AGG_SUM) {
+        acc += prod;
+        return;
+    }
+    if ((uint32_t)v.y < (uint32_t)p.G) {
+        if (GSMEM)
+            add64_split(g.lo + v.y, g.hi + v.y, prod);
+        else
+            atomicAdd(p.out + v.y, prod);
+    } else {
+        raise_error(p.err, kErrGroupRange);
+    }
+}
+
+// CTA epilogue: shared group sums into the output (one global add per nonzero
+// group), or the register sum of COUNT / SUM reduced per warp.
+template <int AGG, bool GSMEM>
+__device__ __forceinline__ void flush_groups(const PP &p, unsigned long long acc, GrpRef g) {
+    if (AGG == SKX_AGG_GROUPBY_SUM) {
+        if (GSMEM) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < p.G; k += blockDim.x) {
+                const unsigned long long v = (unsigned long long)g.lo[k] + ((unsigned long long)g.hi[k] << 32);
+                if (v) atomicAdd(p.out + k, v);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31u) == 0 && acc) atomicAdd(p.out, acc);
+    }
+}
+
 struct HotArrays {
     uint32_t *lo, *lane_lo;
     int32_t *hi, *lane_hi;
 };
+
+// handle() with the 32-bit group sums (the single and split probes).
+template <int AGG, int PATH, bool GSMEM>
+__device__ __forceinline__ void handle_row(const PP &p, int32_t k, int32_t m, const int4 &row, unsigned long long &acc,
+                                           GrpRef g, const HotArrays &h, unsigned lane) {
+    if ((uint32_t)k < (uint32_t)p.t_hot) {
+        if ((uint32_t)k < (uint32_t)p.t_lane) {
+            const size_t i = (size_t(k) << 5) + lane;
+            hot_add<AGG>(HotRef{h.lane_lo + i, h.lane_hi + i}, m);
+        } else {
+            hot_add<AGG>(HotRef{h.lo + k, h.hi + k}, m);
+        }
+    } else if ((uint32_t)k < (uint32_t)p.N) {
+        fold_row<AGG, GSMEM>(p, row, m, acc, g);
+    } else {
+        raise_error(p.err, kErrKeyRange);
+    }
+}
 
 template <int AGG, int PATH, bool GSMEM>
 __device__ __forceinline__ void handle(const PP &p, int32_t k, int32_t m, const int4 &row, unsigned long long &acc,

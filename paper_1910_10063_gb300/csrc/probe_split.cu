@@ -95,7 +95,7 @@ struct Stage {
 // barrier, with the same stage contents.
 template <int AGG, int PATH, bool GSMEM>
 __device__ void flush_stage(const PP &p, const SP &d, const Stage &s, uint64_t pol_g, uint64_t pol_w,
-                            unsigned long long &acc, unsigned long long *s_grp) {
+                            unsigned long long &acc, GrpRef g) {
     const uint32_t n = *s.fill;
     const unsigned lane = lane_id();
     if (threadIdx.x < 32) {
@@ -135,8 +135,7 @@ __device__ void flush_stage(const PP &p, const SP &d, const Stage &s, uint64_t p
         for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
             const int2 v = s.rows[e];
             const int4 row = fetch_row<PATH, AGG>(p, v.x, pol_g);
-            const unsigned long long amount = AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)v.y;
-            fold<AGG, GSMEM>(p, row, amount, acc, s_grp);
+            fold_row<AGG, GSMEM>(p, row, v.y, acc, g);
         }
     }
     __syncthreads();
@@ -150,7 +149,9 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
     extern __shared__ unsigned long long smem[];
     __shared__ uint32_t s_fill, s_misc[4];
     const int ngrp = GSMEM ? p.G : 0;
-    unsigned long long *s_grp = smem;
+    GrpRef g;
+    g.lo = reinterpret_cast<uint32_t *>(smem);
+    g.hi = g.lo + ngrp;
     HotArrays h;
     h.lo = reinterpret_cast<uint32_t *>(smem + ngrp);
     h.hi = reinterpret_cast<int32_t *>(h.lo + p.t_hot);
@@ -240,20 +241,17 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const uint32_t k = (uint32_t)key[j];
-            if (valid && k >= t_hot && k < t_split) {
-                const unsigned long long amount = AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)mea[j];
-                fold<AGG, GSMEM>(p, row[j], amount, acc, s_grp);
-            }
+            if (valid && k >= t_hot && k < t_split) fold_row<AGG, GSMEM>(p, row[j], mea[j], acc, g);
         }
         // The stage's fill after this sub-step is the largest value any warp's
         // reservation returned, so the barrier's OR over those tells every thread
         // the same answer (reading s_fill itself here would race with warps that
         // already reserve for the next sub-step).
         const bool full = lane == 31 && wtot && wbase + wtot >= (uint32_t)kFlushAt;
-        if (__syncthreads_or(full)) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, s_grp);
+        if (__syncthreads_or(full)) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, g);
     }
     __syncthreads();
-    if (s_fill > 0) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, s_grp);
+    if (s_fill > 0) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, g);
 
     // unaligned head (< 4 rows) and ragged tail (< 4 rows): resolved here
     const int64_t tid = cta0 + threadIdx.x;
@@ -267,7 +265,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
             const int32_t m = AGG == SKX_AGG_COUNT ? 0 : p.measure[idx];
             int4 r = make_int4(0, 0, 0, 0);
             if ((uint32_t)k >= t_hot && (uint32_t)k < nkeys) r = fetch_row<PATH, AGG>(p, k, pol_g);
-            handle<AGG, PATH, GSMEM>(p, k, m, r, acc, s_grp, h, lane);
+            handle_row<AGG, PATH, GSMEM>(p, k, m, r, acc, g, h, lane);
         }
     }
     __syncthreads();
@@ -282,27 +280,21 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
         }
         if (sum == 0) continue;
         const int4 v = fetch_row<PATH, AGG>(p, k, pol_g);
-        fold<AGG, GSMEM>(p, v, sum, acc, s_grp);
+        fold_sum<AGG, GSMEM>(p, v, sum, acc, g);
     }
-    if (AGG == SKX_AGG_GROUPBY_SUM) {
-        if (GSMEM) {
-            __syncthreads();
-            for (int g = threadIdx.x; g < p.G; g += blockDim.x)
-                if (s_grp[g]) atomicAdd(p.out + g, s_grp[g]);
-        }
-    } else {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0 && acc) atomicAdd(p.out, acc);
-    }
+    flush_groups<AGG, GSMEM>(p, acc, g);
 }
 
-// Pass 2: the deferred rows, bucket by bucket.
+// Pass 2: the deferred rows, bucket by bucket.  Each lane holds kUnitBatch
+// entries of the current round while the next round's entries load, so a warp
+// keeps two rounds of memory accesses in flight.
 template <int AGG, int PATH, bool GSMEM>
 __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_deferred(PP p, SP d) {
     extern __shared__ unsigned long long smem[];
     const int ngrp = GSMEM ? p.G : 0;
-    unsigned long long *s_grp = smem;
+    GrpRef g;
+    g.lo = reinterpret_cast<uint32_t *>(smem);
+    g.hi = g.lo + ngrp;
     for (int i = threadIdx.x; i < ngrp; i += blockDim.x) smem[i] = 0;
     __syncthreads();
     const uint64_t pol_s = policy_evict_first();
@@ -328,49 +320,39 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_deferred(PP p, SP d)
         const uint32_t incl = warp_incl_scan(c, lane);
         const uint32_t excl = incl - c;
         const uint32_t T = __shfl_sync(0xffffffffu, incl, kRunsPerUnit - 1);
-        for (uint32_t j0 = 0; j0 < T; j0 += 32 * kUnitBatch) {
-            int2 e[kUnitBatch];
-            bool v[kUnitBatch];
+        // entry j of the unit's concatenated runs -> its buffer position
+        auto load_round = [&](uint32_t j0, int2 *e) {
 #pragma unroll
             for (int q = 0; q < kUnitBatch; ++q) {
                 const uint32_t j = j0 + q * 32 + lane;
-                // run of entry j: the number of runs whose inclusive end is <= j
-                uint32_t t = 0;
+                uint32_t t = 0;  // the number of runs whose inclusive end is <= j
                 if (__shfl_sync(0xffffffffu, incl, 3) <= j) t = 4;
                 if (__shfl_sync(0xffffffffu, incl, t + 1) <= j) t += 2;
                 if (__shfl_sync(0xffffffffu, incl, t) <= j) t += 1;
                 const uint32_t rs = __shfl_sync(0xffffffffu, st, t);
                 const uint32_t rx = __shfl_sync(0xffffffffu, excl, t);
-                v[q] = j < T;
                 e[q] = make_int2(0, 0);
-                if (v[q]) e[q] = ld_stream8(d.miss + (size_t(rs) + (j - rx)), pol_s);
+                if (j < T) e[q] = ld_stream8(d.miss + (size_t(rs) + (j - rx)), pol_s);
             }
+        };
+        int2 nxt[kUnitBatch];
+        load_round(0, nxt);
+        for (uint32_t j0 = 0; j0 < T; j0 += 32 * kUnitBatch) {
+            int2 e[kUnitBatch];
             int4 row[kUnitBatch];
 #pragma unroll
             for (int q = 0; q < kUnitBatch; ++q) {
+                e[q] = nxt[q];
                 row[q] = make_int4(0, 0, 0, 0);
-                if (v[q]) row[q] = fetch_row<PATH, AGG>(p, e[q].x, pol_g);
+                if (j0 + q * 32 + lane < T) row[q] = fetch_row<PATH, AGG>(p, e[q].x, pol_g);
             }
+            if (j0 + 32 * kUnitBatch < T) load_round(j0 + 32 * kUnitBatch, nxt);
 #pragma unroll
             for (int q = 0; q < kUnitBatch; ++q)
-                if (v[q]) {
-                    const unsigned long long amount =
-                        AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)e[q].y;
-                    fold<AGG, GSMEM>(p, row[q], amount, acc, s_grp);
-                }
+                if (j0 + q * 32 + lane < T) fold_row<AGG, GSMEM>(p, row[q], e[q].y, acc, g);
         }
     }
-    if (AGG == SKX_AGG_GROUPBY_SUM) {
-        if (GSMEM) {
-            __syncthreads();
-            for (int g = threadIdx.x; g < p.G; g += blockDim.x)
-                if (s_grp[g]) atomicAdd(p.out + g, s_grp[g]);
-        }
-    } else {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0 && acc) atomicAdd(p.out, acc);
-    }
+    flush_groups<AGG, GSMEM>(p, acc, g);
 }
 
 template <typename K>

@@ -192,10 +192,10 @@ def test_split_probe_data_errors(data):
 def test_split_threshold_from_index_matches_oracle_pipeline():
     """skx_split_threshold: counts at log-spaced ranks, the power-law fit and the cache model's
     threshold, recomputed here with the oracle's fit and model on the oracle's counts."""
-    n, f = 2_000_000, 40_000_000
+    n, f = 6000, 600_000  # the oracle's model is O(L^2): keep it to 3000 lines
     w = synth.DeviceWorkload(n, f, 1.0, seed=6, width=1, with_measure=False, with_dim=False)
     idx = skx.skx_build_index(w.fk, n)
-    S_bytes = 8 << 20
+    S_bytes = 400 * 128
     t = skx.skx_split_threshold(idx, 64, S_bytes, 0.5)
     cnt, perm, _ = oracle.build_index(w.fk.cpu().numpy(), n)
     by_rank = cnt[perm].astype(np.float64)
