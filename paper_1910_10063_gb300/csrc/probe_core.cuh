@@ -203,10 +203,86 @@ __device__ __forceinline__ void flush_groups(const PP &p, unsigned long long acc
     }
 }
 
+// Four rows at once: their shared atomics are issued back to back and only
+// then are the returned words inspected, so the atomics' latencies overlap
+// instead of each row waiting for its own before the next one starts.
+template <int AGG, bool GSMEM>
+__device__ __forceinline__ void fold4(const PP &p, const int4 (&v)[4], const int32_t (&m)[4], const bool (&use)[4],
+                                      unsigned long long &acc, GrpRef g) {
+    bool ok[4];
+    unsigned long long prod[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        ok[j] = use[j] && passes(p, v[j]);
+        prod[j] = (unsigned long long)((long long)m[j] * (long long)v[j].z);
+    }
+    if (AGG == SKX_AGG_COUNT) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc += ok[j] ? 1ull : 0ull;
+        return;
+    }
+    if (AGG == SKX_AGG_SUM) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc += ok[j] ? prod[j] : 0ull;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (ok[j] && (uint32_t)v[j].y >= (uint32_t)p.G) {
+            raise_error(p.err, kErrGroupRange);
+            ok[j] = false;
+        }
+    if (!GSMEM) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) atomicAdd(p.out + v[j].y, prod[j]);
+        return;
+    }
+    uint32_t old[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) old[j] = ok[j] ? atomicAdd(g.lo + v[j].y, (uint32_t)prod[j]) : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t xl = (uint32_t)prod[j];
+        const uint32_t inc = (uint32_t)(prod[j] >> 32) + (old[j] + xl < old[j] ? 1u : 0u);
+        if (ok[j] && inc) atomicAdd(g.hi + v[j].y, inc);
+    }
+}
+
 struct HotArrays {
     uint32_t *lo, *lane_lo;
     int32_t *hi, *lane_hi;
 };
+
+// Hot-key adds of four rows (use[j]: key[j] < t_hot), batched like fold4.
+template <int AGG>
+__device__ __forceinline__ void hot_add4(const PP &p, const HotArrays &h, const int32_t (&k)[4],
+                                         const int32_t (&m)[4], const bool (&use)[4], unsigned lane) {
+    uint32_t *lo[4];
+    int32_t *hi[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool ln = (uint32_t)k[j] < (uint32_t)p.t_lane;
+        const size_t li = (size_t(k[j]) << 5) + lane;
+        lo[j] = ln ? h.lane_lo + li : h.lo + k[j];
+        hi[j] = ln ? h.lane_hi + li : h.hi + k[j];
+    }
+    if (AGG == SKX_AGG_COUNT) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (use[j]) atomicAdd(lo[j], 1u);
+        return;
+    }
+    uint32_t old[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) old[j] = use[j] ? atomicAdd(lo[j], (uint32_t)m[j]) : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t u = (uint32_t)m[j];
+        const int d = (int)(old[j] + u < old[j]) - (int)(m[j] < 0);
+        if (use[j] && d) atomicAdd(hi[j], d);
+    }
+}
 
 // handle() with the 32-bit group sums (the single and split probes).
 template <int AGG, int PATH, bool GSMEM>

@@ -13,20 +13,24 @@
 // close to once per probe.
 //
 // Pass 1 (k_probe_split), a persistent grid streaming fk and measure with
-// 16-byte loads, one vector per thread per sub-step:
+// 16-byte loads, one vector (4 rows) per thread per sub-step:
 //   * k < t_hot          per-key shared-memory sums (threshold processing),
 //                        folded once per CTA at the end (as in probe.cu);
 //   * t_hot <= k < t     gathered and folded at once (likely L2 hits);
 //   * t <= k < N         deferred: staged in shared memory with its rank
 //                        within its bucket (bucket = (k - t) >> bshift).
-// After a sub-step that leaves at least kFlushAt rows staged, the CTA
-// reserves room for them in the global buffer (one atomic), lays them out
-// there bucket by bucket, and records each bucket's run in a bucket-major
-// run table (start[b][tau], count[b][tau], tau = the flush's number).  If
-// the buffer or the table is full, the CTA resolves its staged rows itself.
-// Pass 2 (k_probe_deferred): each warp takes units (bucket b, 8 consecutive
-// flushes) from an atomic counter in bucket-major order, concatenates the 8
-// runs, loads 128 entries at a time, gathers their rows and folds them.
+// Each class's shared atomics for the 4 rows are issued together.  After a
+// sub-step that leaves at least kFlushAt rows staged, the CTA lays them out
+// bucket by bucket in its own region of the global buffer (no global
+// atomics: every CTA owns cap / grid entries) and records the flush in a
+// run table: per flush its start in the buffer, and per bucket the run's
+// offset and length packed in one word (bucket-major, so the second pass
+// reads the runs of one bucket contiguously).  A CTA whose region is full
+// resolves its staged rows itself.
+// Pass 2 (k_probe_deferred): each warp takes units (bucket, CTA, 8
+// consecutive flushes of that CTA) from an atomic counter in bucket-major
+// order, concatenates the 8 runs, and resolves them 128 entries per round
+// with the next round's entries already loading.
 // Sums are exact modulo 2^64 in any order, so the result equals probe.cu's.
 #include <algorithm>
 
@@ -40,23 +44,25 @@ using namespace pcore;
 constexpr int kSplitThreads = 512;
 constexpr int kStage = 4096;                          // staged rows per CTA
 constexpr int kFlushAt = kStage - 4 * kSplitThreads;  // one more sub-step always fits
-constexpr int kMaxBuckets = 1024;
+constexpr int kMaxBuckets = 512;
 constexpr int kRunsPerUnit = 8;
-constexpr int kUnitBatch = 4;  // entries per lane per round of pass 2
+constexpr int kUnitBatch = 4;  // entries per lane per round of pass 2 (fold4 takes four)
 
-static_assert(kFlushAt > 0 && kStage <= 65536, "staging sizes");
+static_assert(kFlushAt > 0 && kStage < 65536, "staging sizes (offsets and lengths packed in 16 bits)");
 static_assert(int64_t(kStage) * 10 + int64_t(kMaxBuckets) * 8 <= kSplitSmemBytes, "staging smem budget");
 
 struct SP {
-    int2 *miss;        // deferred (key, measure) rows, cap entries
-    uint32_t cap;
-    uint32_t *tstart;  // [B][max_tiles]
-    uint32_t *tcnt;    // [B][max_tiles]
-    uint32_t max_tiles;
-    uint32_t *ctr;     // [0] rows reserved, [1] flushes numbered, [2] pass-2 units taken
+    int2 *miss;         // deferred (key, measure) rows: CTA c owns [c * region, (c + 1) * region)
+    uint32_t region;    // entries per CTA
+    uint32_t max_flush; // numbered flushes per CTA at most
+    uint32_t *fbase;    // [grid][max_flush] first buffer entry of each flush
+    uint32_t *runs;     // [B][grid][max_flush] run offset (low 16 bits) and length (high 16 bits)
+    uint32_t *nflush;   // [grid] numbered flushes of each CTA
+    uint32_t *ctr;      // [0] largest nflush, [1] pass-2 units taken
     int32_t t_split;
     int32_t bshift;
     int32_t B;
+    int32_t grid;       // CTAs of pass 1
 };
 
 __device__ __forceinline__ void st_evict_first8(int2 *p, int2 v, uint64_t pol) {
@@ -82,23 +88,25 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, unsigned lane) {
 }
 
 struct Stage {
-    int2 *rows;       // kStage entries
-    uint16_t *rank;   // kStage ranks within their bucket
-    uint32_t *cnt;    // B
-    uint32_t *off;    // B
-    uint32_t *fill;   // 1
-    uint32_t *misc;   // base, tau, ok
+    int2 *rows;      // kStage entries
+    uint16_t *rank;  // kStage ranks within their bucket
+    uint32_t *cnt;   // B
+    uint32_t *off;   // B
+    uint32_t *fill;  // staged rows
+    uint32_t *cur;   // [0] entries of the CTA's region used, [1] numbered flushes
 };
 
-// Moves the staged rows to the global buffer (or resolves them here when it is
-// full) and clears the stage.  Called by every thread of the CTA, after a
-// barrier, with the same stage contents.
+// Moves the staged rows into the CTA's region of the global buffer (or
+// resolves them here when the region is full) and clears the stage.  Called
+// by every thread of the CTA after a barrier, with the same stage contents.
 template <int AGG, int PATH, bool GSMEM>
 __device__ void flush_stage(const PP &p, const SP &d, const Stage &s, uint64_t pol_g, uint64_t pol_w,
                             unsigned long long &acc, GrpRef g) {
     const uint32_t n = *s.fill;
-    const unsigned lane = lane_id();
+    const uint32_t used = s.cur[0], k = s.cur[1];
+    const bool ok = used + n <= d.region && k < d.max_flush;
     if (threadIdx.x < 32) {
+        const unsigned lane = lane_id();
         uint32_t carry = 0;
         for (int b0 = 0; b0 < d.B; b0 += 32) {
             const int b = b0 + (int)lane;
@@ -107,31 +115,21 @@ __device__ void flush_stage(const PP &p, const SP &d, const Stage &s, uint64_t p
             if (b < d.B) s.off[b] = carry + incl - c;
             carry += __shfl_sync(0xffffffffu, incl, 31);
         }
-        if (lane == 0) {
-            const uint32_t base = atomicAdd(d.ctr + 0, n);
-            const uint32_t tau = atomicAdd(d.ctr + 1, 1u);
-            s.misc[0] = base;
-            s.misc[1] = tau;
-            s.misc[2] = (uint64_t(base) + n <= uint64_t(d.cap) && tau < d.max_tiles) ? 1u : 0u;
-        }
     }
     __syncthreads();
-    const uint32_t base = s.misc[0], tau = s.misc[1];
-    const bool ok = s.misc[2] != 0;
-    if (tau < d.max_tiles)
-        for (int b = threadIdx.x; b < d.B; b += blockDim.x) {
-            const size_t ti = size_t(b) * d.max_tiles + tau;
-            d.tstart[ti] = base + s.off[b];
-            d.tcnt[ti] = ok ? s.cnt[b] : 0u;
-        }
     if (ok) {
+        const size_t fi = size_t(blockIdx.x) * d.max_flush + k;
+        const uint32_t base = blockIdx.x * d.region + used;
+        if (threadIdx.x == 0) d.fbase[fi] = base;
+        const size_t stride = size_t(d.grid) * d.max_flush;
+        for (int b = threadIdx.x; b < d.B; b += blockDim.x) d.runs[size_t(b) * stride + fi] = s.off[b] | (s.cnt[b] << 16);
         for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
             const int2 v = s.rows[e];
             const int b = (v.x - d.t_split) >> d.bshift;
             st_evict_first8(d.miss + (size_t(base) + s.off[b] + s.rank[e]), v, pol_w);
         }
     } else {
-        // no room left: resolve the staged rows here
+        // no room left in this CTA's region: resolve the staged rows here
         for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
             const int2 v = s.rows[e];
             const int4 row = fetch_row<PATH, AGG>(p, v.x, pol_g);
@@ -140,14 +138,20 @@ __device__ void flush_stage(const PP &p, const SP &d, const Stage &s, uint64_t p
     }
     __syncthreads();
     for (int b = threadIdx.x; b < d.B; b += blockDim.x) s.cnt[b] = 0;
-    if (threadIdx.x == 0) *s.fill = 0;
+    if (threadIdx.x == 0) {
+        *s.fill = 0;
+        if (ok) {
+            s.cur[0] = used + n;
+            s.cur[1] = k + 1;
+        }
+    }
     __syncthreads();
 }
 
 template <int AGG, int PATH, bool GSMEM>
 __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
     extern __shared__ unsigned long long smem[];
-    __shared__ uint32_t s_fill, s_misc[4];
+    __shared__ uint32_t s_fill, s_cur[2];
     const int ngrp = GSMEM ? p.G : 0;
     GrpRef g;
     g.lo = reinterpret_cast<uint32_t *>(smem);
@@ -164,10 +168,14 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
     s.cnt = reinterpret_cast<uint32_t *>(s.rank + kStage);
     s.off = s.cnt + d.B;
     s.fill = &s_fill;
-    s.misc = s_misc;
+    s.cur = s_cur;
     for (int i = threadIdx.x; i < nsm; i += blockDim.x) smem[i] = 0;
     for (int b = threadIdx.x; b < d.B; b += blockDim.x) s.cnt[b] = 0;
-    if (threadIdx.x == 0) s_fill = 0;
+    if (threadIdx.x == 0) {
+        s_fill = 0;
+        s_cur[0] = 0;
+        s_cur[1] = 0;
+    }
     __syncthreads();
 
     const uint64_t pol_s = policy_evict_first();
@@ -193,56 +201,45 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
         const bool valid = i < nvec;
         const int32_t key[4] = {nk.x, nk.y, nk.z, nk.w};
         const int32_t mea[4] = {nm.x, nm.y, nm.z, nm.w};
-        int4 row[4];
+        bool hot[4], direct[4], defer[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const uint32_t k = (uint32_t)key[j];
+            hot[j] = valid && k < t_hot;
+            direct[j] = valid && k >= t_hot && k < t_split;
+            defer[j] = valid && k >= t_split && k < nkeys;
+            if (valid && k >= nkeys) raise_error(p.err, kErrKeyRange);
+        }
+        int4 row[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
             row[j] = make_int4(0, 0, 0, 0);
-            if (valid && k >= t_hot && k < t_split) row[j] = fetch_row<PATH, AGG>(p, key[j], pol_g);
+            if (direct[j]) row[j] = fetch_row<PATH, AGG>(p, key[j], pol_g);
         }
         if (i + nthr < nvec) {
             nk = ld_stream16(fk4 + i + nthr, pol_s);
             if (AGG != SKX_AGG_COUNT) nm = ld_stream16(m4 + i + nthr, pol_s);
         }
-        uint32_t ndef = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t k = (uint32_t)key[j];
-            if (!valid) continue;
-            if (k < t_hot) {
-                if (k < (uint32_t)p.t_lane) {
-                    const size_t li = (size_t(k) << 5) + lane;
-                    hot_add<AGG>(HotRef{h.lane_lo + li, h.lane_hi + li}, mea[j]);
-                } else {
-                    hot_add<AGG>(HotRef{h.lo + k, h.hi + k}, mea[j]);
-                }
-            } else if (k >= t_split) {
-                if (k < nkeys) ++ndef;
-                else raise_error(p.err, kErrKeyRange);
-            }
-        }
+        if (t_hot) hot_add4<AGG>(p, h, key, mea, hot, lane);
         // stage slots for the warp's deferred rows: one shared atomic per warp
+        const uint32_t ndef = (uint32_t)defer[0] + defer[1] + defer[2] + defer[3];
         const uint32_t incl = warp_incl_scan(ndef, lane);
         const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
         uint32_t wbase = 0;
         if (lane == 31 && wtot) wbase = atomicAdd(&s_fill, wtot);
         uint32_t slot = __shfl_sync(0xffffffffu, wbase, 31) + incl - ndef;
+        uint32_t r[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t k = (uint32_t)key[j];
-            if (valid && k >= t_split && k < nkeys) {
-                const uint32_t b = (k - t_split) >> d.bshift;
-                const uint32_t r = atomicAdd(s.cnt + b, 1u);
+        for (int j = 0; j < 4; ++j)
+            r[j] = defer[j] ? atomicAdd(s.cnt + (((uint32_t)key[j] - t_split) >> d.bshift), 1u) : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (defer[j]) {
                 s.rows[slot] = make_int2(key[j], mea[j]);
-                s.rank[slot] = (uint16_t)r;
+                s.rank[slot] = (uint16_t)r[j];
                 ++slot;
             }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t k = (uint32_t)key[j];
-            if (valid && k >= t_hot && k < t_split) fold_row<AGG, GSMEM>(p, row[j], mea[j], acc, g);
-        }
+        fold4<AGG, GSMEM>(p, row, mea, direct, acc, g);
         // The stage's fill after this sub-step is the largest value any warp's
         // reservation returned, so the barrier's OR over those tells every thread
         // the same answer (reading s_fill itself here would race with warps that
@@ -252,6 +249,10 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
     }
     __syncthreads();
     if (s_fill > 0) flush_stage<AGG, PATH, GSMEM>(p, d, s, pol_g, pol_s, acc, g);
+    if (threadIdx.x == 0) {
+        d.nflush[blockIdx.x] = s_cur[1];
+        atomicMax(d.ctr + 0, s_cur[1]);
+    }
 
     // unaligned head (< 4 rows) and ragged tail (< 4 rows): resolved here
     const int64_t tid = cta0 + threadIdx.x;
@@ -263,9 +264,9 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_split(PP p, SP d) {
         if (idx >= 0) {
             const int32_t k = p.fk[idx];
             const int32_t m = AGG == SKX_AGG_COUNT ? 0 : p.measure[idx];
-            int4 r = make_int4(0, 0, 0, 0);
-            if ((uint32_t)k >= t_hot && (uint32_t)k < nkeys) r = fetch_row<PATH, AGG>(p, k, pol_g);
-            handle_row<AGG, PATH, GSMEM>(p, k, m, r, acc, g, h, lane);
+            int4 rw = make_int4(0, 0, 0, 0);
+            if ((uint32_t)k >= t_hot && (uint32_t)k < nkeys) rw = fetch_row<PATH, AGG>(p, k, pol_g);
+            handle_row<AGG, PATH, GSMEM>(p, k, m, rw, acc, g, h, lane);
         }
     }
     __syncthreads();
@@ -301,24 +302,30 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_deferred(PP p, SP d)
     const uint64_t pol_g = policy_by_code(p.gather_policy);
     const unsigned lane = lane_id();
     unsigned long long acc = 0;
-    const uint32_t used = *(volatile uint32_t *)(d.ctr + 1);
-    const uint32_t n_tiles = used < d.max_tiles ? used : d.max_tiles;
-    const uint32_t upb = (n_tiles + kRunsPerUnit - 1) / kRunsPerUnit;  // units per bucket
-    const uint64_t total = uint64_t(upb) * uint64_t(d.B);
+    const uint32_t mf = *(volatile uint32_t *)(d.ctr + 0);
+    const uint32_t most = mf < d.max_flush ? mf : d.max_flush;
+    const uint32_t ku = (most + kRunsPerUnit - 1) / kRunsPerUnit;  // units per CTA per bucket
+    const uint64_t upb = uint64_t(ku) * uint64_t(d.grid);          // units per bucket
+    const uint64_t total = upb * uint64_t(d.B);
+    const size_t stride = size_t(d.grid) * d.max_flush;
     for (;;) {
         uint32_t u = 0;
-        if (lane == 0) u = atomicAdd(d.ctr + 2, 1u);
+        if (lane == 0) u = atomicAdd(d.ctr + 1, 1u);
         u = __shfl_sync(0xffffffffu, u, 0);
         if (uint64_t(u) >= total) break;
-        const uint32_t b = u / upb, tau0 = (u % upb) * kRunsPerUnit;
-        uint32_t c = 0, st = 0;
-        if (lane < (unsigned)kRunsPerUnit && tau0 + lane < n_tiles) {
-            const size_t ti = size_t(b) * d.max_tiles + tau0 + lane;
-            c = d.tcnt[ti];
-            st = d.tstart[ti];
+        const uint32_t b = (uint32_t)(u / upb);
+        const uint32_t rest = (uint32_t)(u % upb);
+        const uint32_t c = rest / ku, k0 = (rest % ku) * kRunsPerUnit;
+        const uint32_t nf = d.nflush[c];
+        uint32_t cn = 0, st = 0;
+        if (lane < (unsigned)kRunsPerUnit && k0 + lane < nf && k0 + lane < d.max_flush) {
+            const size_t fi = size_t(c) * d.max_flush + k0 + lane;
+            const uint32_t w = d.runs[size_t(b) * stride + fi];
+            cn = w >> 16;
+            st = d.fbase[fi] + (w & 0xffffu);
         }
-        const uint32_t incl = warp_incl_scan(c, lane);
-        const uint32_t excl = incl - c;
+        const uint32_t incl = warp_incl_scan(cn, lane);
+        const uint32_t excl = incl - cn;
         const uint32_t T = __shfl_sync(0xffffffffu, incl, kRunsPerUnit - 1);
         // entry j of the unit's concatenated runs -> its buffer position
         auto load_round = [&](uint32_t j0, int2 *e) {
@@ -340,16 +347,18 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_probe_deferred(PP p, SP d)
         for (uint32_t j0 = 0; j0 < T; j0 += 32 * kUnitBatch) {
             int2 e[kUnitBatch];
             int4 row[kUnitBatch];
+            int32_t mea[kUnitBatch];
+            bool use[kUnitBatch];
 #pragma unroll
             for (int q = 0; q < kUnitBatch; ++q) {
                 e[q] = nxt[q];
+                use[q] = j0 + q * 32 + lane < T;
+                mea[q] = e[q].y;
                 row[q] = make_int4(0, 0, 0, 0);
-                if (j0 + q * 32 + lane < T) row[q] = fetch_row<PATH, AGG>(p, e[q].x, pol_g);
+                if (use[q]) row[q] = fetch_row<PATH, AGG>(p, e[q].x, pol_g);
             }
             if (j0 + 32 * kUnitBatch < T) load_round(j0 + 32 * kUnitBatch, nxt);
-#pragma unroll
-            for (int q = 0; q < kUnitBatch; ++q)
-                if (j0 + q * 32 + lane < T) fold_row<AGG, GSMEM>(p, row[q], e[q].y, acc, g);
+            fold4<AGG, GSMEM>(p, row, mea, use, acc, g);
         }
     }
     flush_groups<AGG, GSMEM>(p, acc, g);
@@ -392,25 +401,28 @@ cudaError_t run_split(const PP &p, const skx_tuning &t, int32_t bshift, int32_t 
     d.t_split = t.split_keys;
     d.bshift = bshift;
     d.B = B;
-    // Deferred rows beyond half the column are resolved in pass 1 (if more
-    // than half the rows miss, splitting them off no longer pays).  Flush
-    // numbers: one per kFlushAt reserved rows, a last one per CTA, and up to
-    // one per CTA that raced a failed reservation.
-    const uint64_t cap = std::min<uint64_t>(uint64_t(p.F), uint64_t(p.F) / 2 + uint64_t(kStage) * g1);
-    d.cap = (uint32_t)cap;
-    d.max_tiles = (uint32_t)(cap / kFlushAt + 2 * uint64_t(g1) + 2);
-    const size_t table = size_t(B) * d.max_tiles * 4;
+    d.grid = g1;
+    // Deferred rows beyond about half the column are resolved in pass 1 (if
+    // more than half the rows miss, splitting them off no longer pays): each
+    // CTA owns (F / 2) / grid entries plus one stage.  A numbered flush holds
+    // at least kFlushAt rows except a CTA's last.
+    const uint64_t region = uint64_t(p.F) / 2 / uint64_t(g1) + kStage;
+    d.region = (uint32_t)region;
+    d.max_flush = (uint32_t)(region / kFlushAt + 1);
+    const size_t nfl = size_t(g1) * d.max_flush;
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const size_t off_start = 256, off_cnt = off_start + up(table), off_miss = off_cnt + up(table);
-    const size_t bytes = off_miss + size_t(cap) * 8;
+    const size_t off_nf = 256, off_fb = off_nf + up(size_t(g1) * 4), off_runs = off_fb + up(nfl * 4);
+    const size_t off_miss = off_runs + up(nfl * size_t(B) * 4);
+    const size_t bytes = off_miss + size_t(region) * g1 * 8;
     char *w = nullptr;
     if (cudaMallocAsync(reinterpret_cast<void **>(&w), bytes, st) != cudaSuccess) {
         cudaGetLastError();
         return cudaSuccess;
     }
     d.ctr = reinterpret_cast<uint32_t *>(w);
-    d.tstart = reinterpret_cast<uint32_t *>(w + off_start);
-    d.tcnt = reinterpret_cast<uint32_t *>(w + off_cnt);
+    d.nflush = reinterpret_cast<uint32_t *>(w + off_nf);
+    d.fbase = reinterpret_cast<uint32_t *>(w + off_fb);
+    d.runs = reinterpret_cast<uint32_t *>(w + off_runs);
     d.miss = reinterpret_cast<int2 *>(w + off_miss);
     *ran = true;
     e = cudaMemsetAsync(d.ctr, 0, 16, st);
