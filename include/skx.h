@@ -313,7 +313,7 @@ typedef struct skx_tuning {
                               (otherwise the probe runs unsplit); uses stream-ordered scratch of
                               about 4 F bytes (deferred rows beyond F/2 are resolved at once). */
     int32_t split_bucket;  /* log2 of the ranks per bucket of the second pass (default 19, range
-                              12..26; raised until there are at most 1024 buckets) */
+                              12..26; raised until there are at most 512 buckets) */
     int32_t reserved[7];
 } skx_tuning;
 
@@ -326,6 +326,13 @@ skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes,
  * one, else the defaults), written to *out. */
 skx_status skx_probe_default_tuning(int32_t N, int32_t row_bytes, int64_t F, const skx_query *q,
                                     int remapped, skx_tuning *out);
+
+/* The tuning skx_probe_aggregate resolves *in to for these arguments (every
+ * default filled in; a split threshold outside (hot_keys, N) turned off; the
+ * split's bucket size raised until there are at most 512 buckets), written to
+ * *out.  Host only: it launches nothing. */
+skx_status skx_probe_resolve_tuning(int32_t N, int32_t row_bytes, int64_t F, const skx_query *q,
+                                    const skx_tuning *in, skx_tuning *out);
 
 /*
  * Autotuner for the probe (threshold-based processing, Section IV-B, picks t
@@ -418,6 +425,14 @@ skx_status skx_powerlaw_fit(const double *h_x, const double *h_y, int64_t n, dou
  * two nonzero counts), SKX_ENOMEM, SKX_ECUDA. */
 skx_status skx_split_threshold(const skx_index *idx, int32_t row_bytes, int64_t cache_bytes, double p, int64_t *t,
                                void *stream);
+/* The host half of skx_split_threshold for a fitted exponent (log count =
+ * intercept + slope * log(rank + 1)): frequencies proportional to
+ * (r + 1)^slope for r < N, summed per 128-byte line of rows of row_bytes,
+ * and t from skx_cache_threshold over cache_bytes / 128 lines, capped at N.
+ * Host only.  Errors: SKX_EINVAL (null t, N < 1, bad row_bytes, cache_bytes
+ * below one line, p outside (0, 1], a slope that is not finite). */
+skx_status skx_split_threshold_from_fit(double slope, int32_t N, int32_t row_bytes, int64_t cache_bytes, double p,
+                                        int64_t *t);
 
 /* Counts of chosen ranks of an index, the input of a frequency fit:
  * h_counts[k] = counts[perm[h_ranks[k]]] (the count of the id with
@@ -534,9 +549,11 @@ void skx_server_destroy(skx_server *s);
 /* ------------------------------------------------------------------------
  * Whole path from host memory (Sections III-A, III-B and IV in sequence):
  * copies h_fk[F], h_measure[F] and the dimension table h_rows[N * row_bytes]
- * to the device, builds the index, remaps the keys, reorders the rows,
- * runs the query on the reordered layout and copies the result (num_groups
- * or 1 int64) to h_out.  Device buffers are stream-ordered allocations on
+ * to the device, builds the index, remaps the keys, builds the query's
+ * permuted copy of the dimension rows (skx_reorder_query: 8 bytes per row,
+ * Section III-B), runs the query on it and copies the result (num_groups
+ * or 1 int64) to h_out.  The probe uses the autotuner's cached choice for
+ * (N, 8-byte rows, the prefiltered query) when there is one.  Device buffers are stream-ordered allocations on
  * `stream`, released before return.  Synchronous: returns after h_out is
  * written, with any data error of this call already reported (SKX_EKEYRANGE,
  * SKX_EGROUPRANGE) rather than left for skx_stream_status.

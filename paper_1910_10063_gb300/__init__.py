@@ -145,6 +145,9 @@ def lib():
             L.skx_probe_default_tuning.argtypes = [i32, i32, i64, ctypes.POINTER(Query), ctypes.c_int,
                                                    ctypes.POINTER(Tuning)]
             L.skx_probe_default_tuning.restype = st
+            L.skx_probe_resolve_tuning.argtypes = [i32, i32, i64, ctypes.POINTER(Query), ctypes.POINTER(Tuning),
+                                                   ctypes.POINTER(Tuning)]
+            L.skx_probe_resolve_tuning.restype = st
             L.skx_probe_autotune.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), ctypes.c_int, P, P,
                                              ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_float)]
             L.skx_probe_autotune.restype = st
@@ -154,6 +157,9 @@ def lib():
             L.skx_probe_autotune_ex.restype = st
             L.skx_split_threshold.argtypes = [P, i32, i64, ctypes.c_double, ctypes.POINTER(i64), P]
             L.skx_split_threshold.restype = st
+            L.skx_split_threshold_from_fit.argtypes = [ctypes.c_double, i32, i32, i64, ctypes.c_double,
+                                                       ctypes.POINTER(i64)]
+            L.skx_split_threshold_from_fit.restype = st
             L.skx_batch_plan_create.argtypes = [P, i32, i32, ctypes.POINTER(ProbeDesc), i32, ctypes.POINTER(Tuning), i32,
                                                 P, ctypes.POINTER(P)]
             L.skx_batch_plan_create.restype = st
@@ -451,6 +457,22 @@ def skx_probe_autotune(rows, fk, measure, query: Query, remapped: bool = True, o
                                        _dptr(out, "out", torch.int64), _stream(stream), ctypes.byref(t),
                                        ctypes.byref(ms)), "skx_probe_autotune_ex")
     return t, ms.value
+
+
+def skx_probe_resolve_tuning(n: int, row_bytes: int, f: int, query: Query, tuning: Tuning) -> Tuning:
+    """The tuning the probe resolves `tuning` to (host only)."""
+    out = Tuning()
+    _check(lib().skx_probe_resolve_tuning(int(n), int(row_bytes), int(f), ctypes.byref(query), ctypes.byref(tuning),
+                                          ctypes.byref(out)), "skx_probe_resolve_tuning")
+    return out
+
+
+def skx_split_threshold_from_fit(slope: float, n: int, row_bytes: int, cache_bytes: int, p: float = 0.5) -> int:
+    """Host half of skx_split_threshold: the model's t for counts proportional to (rank + 1)^slope."""
+    t = ctypes.c_int64()
+    _check(lib().skx_split_threshold_from_fit(float(slope), int(n), int(row_bytes), int(cache_bytes), float(p),
+                                              ctypes.byref(t)), "skx_split_threshold_from_fit")
+    return t.value
 
 
 def skx_split_threshold(index: "Index", row_bytes: int, cache_bytes: int = 0, p: float = 0.5, stream=None) -> int:

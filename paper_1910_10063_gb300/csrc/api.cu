@@ -470,6 +470,22 @@ skx_status skx_probe_default_tuning(int32_t N, int32_t row_bytes, int64_t F, con
     return SKX_OK;
 }
 
+skx_status skx_probe_resolve_tuning(int32_t N, int32_t row_bytes, int64_t F, const skx_query *q,
+                                    const skx_tuning *in, skx_tuning *out) {
+    if (!out || !in || N < 1 || F < 0) return SKX_EINVAL;
+    skx_status s = validate_query(q, row_bytes);
+    if (s != SKX_OK) return s;
+    ProbeArgs a{};
+    a.N = N;
+    a.row_bytes = row_bytes;
+    a.F = F;
+    a.q = *q;
+    skx_tuning t = *in;
+    resolve_probe_tuning(a, t);
+    *out = t;
+    return SKX_OK;
+}
+
 skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
                                const int32_t *d_measure, int64_t F, const skx_query *q, int64_t *d_out,
                                const skx_tuning *tuning, void *stream) {
@@ -534,8 +550,10 @@ skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_by
     int64_t *d_out = nullptr;
     skx_index *idx = nullptr;
     cudaEvent_t ev_alloc = nullptr, ev_fk = nullptr, ev_rows = nullptr, ev_done = nullptr, ev_m[kChunks] = {};
+    // the probe runs over the query's own permuted copy (Section III-B): 8 bytes per
+    // dimension row, {group or the filter's sentinel, payload}
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows), rows_b, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows2), rows_b, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows2), size_t(N) * 8, st);
     if (e == cudaSuccess && F > 0) e = cudaMallocAsync(reinterpret_cast<void **>(&d_fk), fk_b, st);
     if (e == cudaSuccess && with_m) e = cudaMallocAsync(reinterpret_cast<void **>(&d_m), fk_b, st);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_out), size_t(nout) * 8, st);
@@ -567,17 +585,17 @@ skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_by
     if (s == SKX_OK) s = skx_build_index(d_fk, F, N, stream, &idx);
     if (s == SKX_OK) s = skx_remap(idx, d_fk, d_fk, F, stream);
     if (s == SKX_OK) s = cudaStreamWaitEvent(st, ev_rows, 0) == cudaSuccess ? SKX_OK : SKX_ECUDA;
-    if (s == SKX_OK) s = skx_reorder(idx, d_rows, d_rows2, N, row_bytes, stream);
+    if (s == SKX_OK) s = skx_reorder_query(idx, d_rows, N, row_bytes, q, d_rows2, stream);
     if (s == SKX_OK) {
         ProbeArgs a{};
         a.rows = d_rows2;
         a.N = N;
-        a.row_bytes = row_bytes;
-        a.q = *q;
+        a.row_bytes = 8;
+        a.q = skx_query_prefiltered(q);
         a.out = d_out;
         a.err = err;
         skx_tuning t{};
-        cached_probe_tuning(N, row_bytes, *q, F, 1, &t);
+        cached_probe_tuning(N, 8, a.q, F, 1, &t);
         const int parts = with_m ? nm : 1;
         for (int k = 0; k < parts && s == SKX_OK; ++k) {
             const int64_t a0 = with_m ? cut(k) : 0, a1 = with_m ? cut(k + 1) : F;

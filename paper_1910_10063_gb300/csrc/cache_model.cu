@@ -174,6 +174,7 @@ skx_status skx_split_threshold(const skx_index *idx, int32_t row_bytes, int64_t 
     const int32_t N = skx_index_size(idx);
     if (N < 2) return SKX_EINVAL;
     constexpr int64_t kLine = 128;
+    if (cache_bytes > 0 && cache_bytes < kLine) return SKX_EINVAL;
     if (cache_bytes == 0) {
         int dev = 0, l2 = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
@@ -201,6 +202,19 @@ skx_status skx_split_threshold(const skx_index *idx, int32_t row_bytes, int64_t 
     double slope = 0.0, icpt = 0.0;
     st = skx_powerlaw_fit(x.data(), y.data(), int64_t(x.size()), &slope, &icpt);
     if (st != SKX_OK) return st;
+    return skx_split_threshold_from_fit(slope, N, row_bytes, S * kLine, p, t);
+}
+
+// The host half of skx_split_threshold: frequencies proportional to
+// (r + 1)^slope over ranks r < N, summed per 128-byte line of the remapped
+// table, and the model's threshold over S = cache_bytes / 128 lines.
+skx_status skx_split_threshold_from_fit(double slope, int32_t N, int32_t row_bytes, int64_t cache_bytes, double p,
+                                        int64_t *t) {
+    constexpr int64_t kLine = 128;
+    if (!t || N < 1 || row_bytes < 4 || row_bytes % 4 != 0 || cache_bytes < kLine || !(p > 0.0 && p <= 1.0) ||
+        !std::isfinite(slope))
+        return SKX_EINVAL;
+    const int64_t S = cache_bytes / kLine;
     const int32_t rows_per_line = std::max<int32_t>(1, int32_t(kLine / row_bytes));
     const int64_t L = (int64_t(N) + rows_per_line - 1) / rows_per_line;
     std::vector<double> f(L, 0.0);
@@ -212,7 +226,7 @@ skx_status skx_split_threshold(const skx_index *idx, int32_t row_bytes, int64_t 
     }
     if (!(total > 0.0)) return SKX_EINVAL;
     for (double &v : f) v /= total;
-    st = skx_cache_threshold(f.data(), L, S, p, rows_per_line, t);
+    const skx_status st = skx_cache_threshold(f.data(), L, S, p, rows_per_line, t);
     if (st == SKX_OK && *t > N) *t = N;
     return st;
 }

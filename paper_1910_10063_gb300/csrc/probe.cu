@@ -221,6 +221,12 @@ void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t) {
     if (t.gather_policy < 1 || t.gather_policy > 4) t.gather_policy = 2;
     if (t.split_bucket < 12 || t.split_bucket > 26) t.split_bucket = 19;
     if (t.split_keys <= 0 || t.split_keys >= a.N) t.split_keys = -1;
+    {
+        // the split's staging must fit beside the group sums in one CTA
+        const bool grp = a.q.agg == SKX_AGG_GROUPBY_SUM;
+        const int64_t gbytes = (grp && a.q.num_groups <= kMaxSmemGroups) ? int64_t(a.q.num_groups) * 8 : 0;
+        if (t.split_keys > 0 && gbytes + kSplitSmemBytes + 1024 > device_max_smem_optin()) t.split_keys = -1;
+    }
     resolve_hot(a, t, t.split_keys > 0 ? kSplitSmemBytes : 0);
     // the split needs keys [hot_keys, split_keys) to exist
     const int32_t hot = t.hot_keys > 0 ? t.hot_keys : 0;
@@ -246,6 +252,11 @@ void resolve_hot(const ProbeArgs &a, skx_tuning &t, int64_t other_smem) {
         t.hot_keys = (int32_t)(((budget - gbytes - int64_t(t.lane_keys) * 256) / 8) & ~int64_t(1023));
     }
     const int64_t room = (optin - 1024 - gbytes - other_smem) / 8;  // 8 bytes per hot key, 256 per lane key
+    if (room < 1 || t.hot_keys < 1) {  // no shared memory left for a hot prefix
+        t.hot_keys = -1;
+        t.lane_keys = -1;
+        return;
+    }
     t.hot_keys = clamp32(t.hot_keys, 1, a.N);
     t.lane_keys = clamp32(t.lane_keys, 0, t.hot_keys);
     if (int64_t(t.hot_keys) + int64_t(t.lane_keys) * 32 > room) {

@@ -11,8 +11,8 @@ namespace pcore {
 
 constexpr int kMaxSmemGroups = 4096;
 // dynamic shared memory of the split probe's first pass beside groups and hot
-// prefix: 4096 staged rows of 10 bytes and two words per bucket (<= 1024)
-constexpr int64_t kSplitSmemBytes = 4096 * 10 + 1024 * 8;
+// prefix: 4096 staged rows of 10 bytes and two words per bucket (<= 512)
+constexpr int64_t kSplitSmemBytes = 4096 * 10 + 512 * 8;
 
 struct PP {
     const int32_t *fk, *measure;

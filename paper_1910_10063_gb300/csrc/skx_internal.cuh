@@ -216,7 +216,7 @@ struct ProbeArgs {
 // Resolves defaults in `t` (in place) for these arguments.
 void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t);
 // Buckets of the split probe's second pass for keys [t_split, N): raises
-// *bshift until there are at most 1024 of them, returns their number.
+// *bshift until there are at most 512 of them, returns their number.
 int32_t split_buckets(int32_t N, int32_t t_split, int32_t *bshift);
 cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t st);
 skx_status validate_query(const skx_query *q, int32_t row_bytes);

@@ -61,3 +61,68 @@ def test_powerlaw_fit_equals_oracle():
         skx.skx_powerlaw_fit([1.0], [1.0])
     with pytest.raises(skx.SkxError):
         skx.skx_cache_threshold([0.5, 0.5], 1, 0.0, 1)
+
+
+def test_split_threshold_from_fit_equals_oracle_pipeline():
+    """The model-derived split threshold (Sections III-C and IV-B): frequencies from a fitted
+    power law summed per 128-byte line, then the model's threshold, against the oracle's model on
+    the same lines."""
+    for n, row_bytes, slope, S, p in ((6000, 64, -1.0, 400, 0.5), (4000, 16, -1.3, 150, 0.5),
+                                      (3001, 64, -0.8, 700, 0.75), (2048, 128, -1.5, 64, 0.5)):
+        rpl = max(1, 128 // row_bytes)
+        fr = np.arange(1, n + 1, dtype=np.float64) ** slope
+        pad = np.zeros(-(-n // rpl) * rpl)
+        pad[:n] = fr
+        lines = pad.reshape(-1, rpl).sum(axis=1) / fr.sum()
+        _, cdf = oracle.cache_hit_rate(lines, S)
+        if np.any(np.abs(cdf - p) < 1e-9):
+            continue
+        want = min(n, oracle.cache_threshold(lines, S, p, rpl))
+        assert skx.skx_split_threshold_from_fit(slope, n, row_bytes, S * 128, p) == want
+    # a bigger cache never gives a smaller threshold; a stricter p never a larger one
+    t1 = skx.skx_split_threshold_from_fit(-1.0, 20_000, 64, 256 * 128, 0.5)
+    assert skx.skx_split_threshold_from_fit(-1.0, 20_000, 64, 1024 * 128, 0.5) >= t1
+    assert skx.skx_split_threshold_from_fit(-1.0, 20_000, 64, 256 * 128, 0.9) <= t1
+    for bad in ((float("nan"), 100, 64, 1 << 20, 0.5), (-1.0, 0, 64, 1 << 20, 0.5), (-1.0, 100, 6, 1 << 20, 0.5),
+                (-1.0, 100, 64, 64, 0.5), (-1.0, 100, 64, 1 << 20, 0.0)):
+        with pytest.raises(skx.SkxError):
+            skx.skx_split_threshold_from_fit(*bad)
+
+
+def test_model_threshold_is_what_the_probe_resolves():
+    """The split threshold from the model is kept as given when the probe resolves its tuning,
+    with the bucket size raised until at most 512 buckets cover the keys above it; a threshold
+    outside (hot_keys, N) turns the split off."""
+    q = skx.Query.sum()  # no group sums: the split's staging fits even the 48 KB a CPU-only process assumes
+    n = 20_000_000
+    t_model = skx.skx_split_threshold_from_fit(-1.0, n, 64, 88_000_000, 0.5)
+    assert 0 < t_model < n
+    tun = skx.Tuning()
+    tun.split_keys = t_model
+    tun.hot_keys = -1
+    r = skx.skx_probe_resolve_tuning(n, 64, 500_000_000, q, tun)
+    assert r.split_keys == t_model
+    assert -(-(n - t_model) // (1 << r.split_bucket)) <= 512 and r.split_bucket >= 19
+    big = skx.Tuning()
+    big.split_keys = 100
+    big.split_bucket = 12
+    r = skx.skx_probe_resolve_tuning(400_000_000, 64, 500_000_000, q, big)
+    assert -(-(400_000_000 - 100) // (1 << r.split_bucket)) <= 512 < -(-(400_000_000 - 100) // (1 << (r.split_bucket - 1)))
+    for t_bad, hot in ((n, -1), (n + 5, -1), (50, 64)):
+        x = skx.Tuning()
+        x.split_keys = t_bad
+        x.hot_keys = hot
+        assert skx.skx_probe_resolve_tuning(n, 64, 500_000_000, q, x).split_keys == -1
+    again = skx.skx_probe_resolve_tuning(n, 64, 500_000_000, q, r)
+    assert again.split_keys == r.split_keys and again.split_bucket == r.split_bucket  # idempotent
+    # whatever the shared memory, a resolved hot prefix is a real size or off, never negative
+    g = skx.Query.groupby_sum(num_groups=4096)
+    for hot in (0, 64, 100_000):
+        x = skx.Tuning()
+        x.hot_keys = hot
+        x.split_keys = 1000
+        r = skx.skx_probe_resolve_tuning(n, 64, 500_000_000, g, x)
+        assert r.hot_keys == -1 or r.hot_keys >= 1
+        assert r.split_keys in (-1, 1000)
+        if r.split_keys == 1000:
+            assert r.hot_keys < 1000
