@@ -3,9 +3,11 @@
 
 A step is one pass of the whole path over the 20M x 64-byte dimension table
 and 500M-row Zipf(s=1.0) FK column: count (Q3) -> sort by frequency ->
-remap the fact keys -> reorder the dimension rows -> FK-join probe with
-filter and GROUP BY SUM.  Inputs are seeded synthetic data generated on the
-device; they are resident in HBM when the timed region starts.
+remap the fact keys -> the query's permuted copy of the dimension rows
+(Section III-B: 8 bytes a row, the filter folded in) -> FK-join probe with
+GROUP BY SUM.  The same path over whole reordered 64-byte rows is timed
+beside it (alt_step_whole_rows).  Inputs are seeded synthetic data generated
+on the device; they are resident in HBM when the timed region starts.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -83,6 +85,8 @@ def config_of(a, world):
                   "fact inputs (4 GB/step) are also far larger than L2",
             "parallelism": "single GPU" if world == 1 else f"{world} independent replicas",
             "count_method": getattr(a, "count_method", "auto"),
+            "dimension_copy": "the query's permuted 8-byte copy {group or sentinel, payload0} (Section III-B); "
+                              "whole 64-byte rows in alt_step_whole_rows",
             "probe_tuning": "autotuned" if not getattr(a, "tuning", "") else a.tuning}
 
 
@@ -132,11 +136,6 @@ COUNT_METHODS = {"auto": 0, "single": 1, "partitioned": 2}
 # uniform keys (s = 0) miss with probability 1 - S/L under LRU, and their measured DRAM line
 # fetches give S = 82-91 MB at N = 2M..20M (profiles/probe_layouts_dram_N1M-20M_500M.txt).
 EFFECTIVE_L2_BYTES = 88_000_000
-# Random 128-byte DRAM line fetches per second that the probe reaches on a 20M x 64 B table
-# (uniform keys, where nearly every gather misses: 464M fetches in 11.2 ms, less the 4 GB of
-# fact columns at the HBM peak; profiles/probe_layouts_dram_N1M-20M_500M.txt).  Smaller tables
-# reach more (49 G/s at 8M rows, 56 G/s at 4M: fewer DRAM pages and TLB entries in play).
-FETCH_RATE_20Mx64B = 44.0e9
 
 
 def count_kernels(fk, n, f, method="auto"):
@@ -241,21 +240,46 @@ def run_ours(a, rank, world, local_rank):
 
     stages = ["count", "sort", "remap", "reorder", "probe"]
 
-    # probe launch shape and hot-prefix size: chosen once by the library's autotuner on
-    # this data (setup, outside the timed region)
+    # Probe launch shapes, hot-prefix sizes and split thresholds: chosen once by the library's
+    # autotuner on this data (setup, outside the timed region).  The split candidates come from
+    # the Section III-C model's threshold for each layout (skx_split_threshold on the index).
+    qp = skx.skx_query_prefiltered(q)
+    q8 = torch.empty((a.n, 2), dtype=torch.int32, device=dev)
     idx0 = skx.skx_build_index(w.fk, a.n)
     skx.skx_remap(idx0, w.fk, fk2)
     skx.skx_reorder(idx0, w.dim, dim2)
+    skx.skx_reorder_query(idx0, w.dim, q, out=q8)
+    t_model = {"query8": skx.skx_split_threshold(idx0, 8), "rows64": skx.skx_split_threshold(idx0, a.width * 4)}
     if a.tuning:
         tuning = skx.Tuning()
         for kv in a.tuning.split(","):
             k, v = kv.split("=")
             setattr(tuning, k.strip(), int(v))
+        tuning_rows = tuning
     else:
-        tuning, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True)
+        tuning, _ = skx.skx_probe_autotune(q8, fk2, w.measure, qp, remapped=True, split_hint=t_model["query8"])
+        tuning_rows, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True,
+                                                split_hint=t_model["rows64"])
     idx0.close()
 
+    # The timed step: the query's own permuted copy of the dimension rows (Section III-B: a copy
+    # of the needed columns, permuted by the index; 8 bytes per row, the filter folded in).
     def step(ev):
+        ev[0].record(stream)
+        skx.skx_count_ex(w.fk, a.n, COUNT_METHODS[a.count_method], counts=counts)
+        ev[1].record(stream)
+        idx = skx.skx_build_index_from_counts(counts, a.f)
+        ev[2].record(stream)
+        skx.skx_remap(idx, w.fk, fk2)
+        ev[3].record(stream)
+        skx.skx_reorder_query(idx, w.dim, q, out=q8)
+        ev[4].record(stream)
+        skx.skx_probe_aggregate(q8, fk2, w.measure, qp, out=out, tuning=tuning)
+        ev[5].record(stream)
+        return idx
+
+    # The same path over whole reordered 64-byte rows (the alternative line).
+    def step_rows(ev):
         ev[0].record(stream)
         skx.skx_count_ex(w.fk, a.n, COUNT_METHODS[a.count_method], counts=counts)
         ev[1].record(stream)
@@ -265,7 +289,7 @@ def run_ours(a, rank, world, local_rank):
         ev[3].record(stream)
         skx.skx_reorder(idx, w.dim, dim2)
         ev[4].record(stream)
-        skx.skx_probe_aggregate(dim2, fk2, w.measure, q, out=out, tuning=tuning)
+        skx.skx_probe_aggregate(dim2, fk2, w.measure, q, out=out, tuning=tuning_rows)
         ev[5].record(stream)
         return idx
 
@@ -300,90 +324,66 @@ def run_ours(a, rank, world, local_rank):
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
     result = out.cpu().numpy().copy()
 
-    # ---------------- the same path with the query-specific 8-byte copy (Section III-B)
-    qp = skx.skx_query_prefiltered(q)
-    q8 = torch.empty((a.n, 2), dtype=torch.int32, device=dev)
-    idx0 = skx.skx_build_index(w.fk, a.n)
-    skx.skx_remap(idx0, w.fk, fk2)
-    skx.skx_reorder_query(idx0, w.dim, q, out=q8)
-    tuning_q8, _ = skx.skx_probe_autotune(q8, fk2, w.measure, qp, remapped=True)
-    idx0.close()
-
-    def step_q8(ev):
-        ev[0].record(stream)
-        skx.skx_count_ex(w.fk, a.n, COUNT_METHODS[a.count_method], counts=counts)
-        ev[1].record(stream)
-        idx = skx.skx_build_index_from_counts(counts, a.f)
-        ev[2].record(stream)
-        skx.skx_remap(idx, w.fk, fk2)
-        ev[3].record(stream)
-        skx.skx_reorder_query(idx, w.dim, q, out=q8)
-        ev[4].record(stream)
-        skx.skx_probe_aggregate(q8, fk2, w.measure, qp, out=out, tuning=tuning_q8)
-        ev[5].record(stream)
-        return idx
-
+    # ---------------- the same path over whole 64-byte rows
     for _ in range(a.warmup):
         flush.zero_()
-        step_q8(new_events()).close()
-    evs8 = [new_events() for _ in range(a.steps)]
+        step_rows(new_events()).close()
+    evsr = [new_events() for _ in range(a.steps)]
     keep = []
     torch.cuda.synchronize()
     for k in range(a.steps):
         flush.zero_()
-        keep.append(step_q8(evs8[k]))
+        keep.append(step_rows(evsr[k]))
     torch.cuda.synchronize()
     for idx in keep:
         idx.close()
     if not np.array_equal(out.cpu().numpy(), result):
-        raise RuntimeError("query-copy path disagrees with the whole-row path")
-    ms8 = sum(e[0].elapsed_time(e[5]) for e in evs8)
-    alt_step = {"reorder": "query-specific 8-byte copy {group or sentinel, payload0} (filter applied per dimension row)",
-                "value": round(a.f * a.steps / (ms8 * 1e-3) / 1e9, 3), "unit": UNIT,
-                "ms_per_step": round(ms8 / a.steps, 4),
-                "stages_ms": {s_: round(statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs8), 4)
-                              for i, s_ in enumerate(stages)},
-                "probe_tuning": {k: tuning_q8.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
-                                                                       "hot_keys", "lane_keys")}}
-    del q8
+        raise RuntimeError("whole-row path disagrees with the query-copy path")
+    msr = sum(e[0].elapsed_time(e[5]) for e in evsr)
+    rows_stage = {s_: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evsr) for i, s_ in enumerate(stages)}
+    Dr = expected_distinct(a.n, a.f, a.s)
+    peak0, _ = hbm_peak()
+    alt_step = {"reorder": "whole 64-byte rows (skx_reorder), probe over them",
+                "value": round(a.f * a.steps / (msr * 1e-3) / 1e9, 3), "unit": UNIT,
+                "ms_per_step": round(msr / a.steps, 4),
+                "stages_ms": {k_: round(v_, 4) for k_, v_ in rows_stage.items()},
+                "probe_alg_bytes": int(8 * a.f + 16 * Dr),
+                "probe_frac": round((8 * a.f + 16 * Dr) / (rows_stage["probe"] * 1e-3) / 1e9 / peak0, 4),
+                "probe_tuning": {k: tuning_rows.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
+                                                                         "hot_keys", "lane_keys", "split_keys")},
+                "split_model_t": t_model["rows64"]}
 
     # ---------------- roofline of the dominant kernel
     peak, peak_src = hbm_peak()
     D = expected_distinct(a.n, a.f, a.s)
-    row_b = a.width * 4
+    probe_kernel = "k_probe_split+k_probe_deferred" if tuning.split_keys > 0 else "k_probe"
+    # reorder_query reads three 4-byte columns and a perm entry per row and writes 8 bytes;
+    # the probe streams fk and measure (8 bytes a row) and gathers 8 bytes per distinct row
     alg = {"count": 4 * a.f + 4 * a.n, "sort": 12 * a.n, "remap": 8 * a.f + 4 * a.n,
-           "reorder": 2 * row_b * a.n + 4 * a.n, "probe": 8 * a.f + 16 * D}
-    kernel_of = {"count": count_kernels(w.fk, a.n, a.f, a.count_method), "sort": "k_radix_*", "remap": "k_remap", "reorder": "k_reorder16",
-                 "probe": "k_probe"}
+           "reorder": 24 * a.n, "probe": 8 * a.f + 8 * D}
+    kernel_of = {"count": count_kernels(w.fk, a.n, a.f, a.count_method), "sort": "k_radix_*", "remap": "k_remap",
+                 "reorder": "k_reorder_query", "probe": probe_kernel}
+    traffic_key = {"count": kernel_of["count"], "sort": "k_radix_*", "remap": "k_remap",
+                   "reorder": "k_reorder_query", "probe": "+".join(k + "/query8" for k in probe_kernel.split("+"))}
     stage_avg = {s: statistics.mean(v) for s, v in stage_ms.items()}
     stage_rep = {s: {"ms": round(stage_avg[s], 4), "alg_bytes": int(alg[s]),
                      "gbs": round(alg[s] / (stage_avg[s] * 1e-3) / 1e9, 1),
                      "frac": round(alg[s] / (stage_avg[s] * 1e-3) / 1e9 / peak, 4),
-                     "kernel": kernel_of[s], "dram_bytes": ncu_traffic(kernel_of[s], a)} for s in stages}
+                     "kernel": kernel_of[s], "dram_bytes": ncu_traffic(traffic_key[s], a)} for s in stages}
     dom = max(stages, key=lambda s: stage_avg[s])
     achieved = alg[dom] / (stage_avg[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kernel_of[dom], "stage": dom, "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} hbm_gbs",
-                "alg_bytes_per_launch": int(alg[dom]), "traffic": ncu_traffic(kernel_of[dom], a),
+                "alg_bytes_per_launch": int(alg[dom]), "traffic": ncu_traffic(traffic_key[dom], a),
                 "algorithmic_bytes": {"count": "4F + 4N", "sort": "12N (read counts, write perm and rank)",
-                                      "remap": "8F + 4N", "reorder": "2*row_bytes*N + 4N",
-                                      "probe": f"8F + 16*D, D = expected distinct keys = {D:.4g}"}[dom]}
+                                      "remap": "8F + 4N", "reorder": "24N (3 columns + perm read, 8 B written)",
+                                      "probe": f"8F + 8*D (8-byte query rows), D = expected distinct keys = {D:.4g}"}[dom]}
     if roofline["traffic"]:
-        # the same launch measured on its actual DRAM bytes (ncu capture of this workload)
+        # the same launch measured on its actual DRAM bytes (ncu capture, scaled to this workload)
         tgbs = roofline["traffic"] / (stage_avg[dom] * 1e-3) / 1e9
         roofline["traffic_gbs"] = round(tgbs, 1)
         roofline["traffic_frac"] = round(tgbs / peak, 4)
-        if dom == "probe" and a.width * 4 == 64 and a.n == 20_000_000:
-            # what bounds this probe: random 128-byte line fetches (their rate, not their
-            # bytes), beside the fact columns' stream at the HBM peak
-            fact_bytes = 8 * a.f
-            fetches = (roofline["traffic"] - fact_bytes) / 128
-            floor_ms = 1e3 * (fetches / FETCH_RATE_20Mx64B + fact_bytes / (peak * 1e9))
-            roofline["line_fetch_bound"] = {
-                "line_fetches": int(fetches), "ceiling_per_s": FETCH_RATE_20Mx64B,
-                "floor_ms": round(floor_ms, 3), "frac": round(floor_ms / stage_avg[dom], 4),
-                "ceiling_source": "uniform keys over this 20M x 64 B table: 464M line fetches in 11.2 ms "
-                                  "less the fact stream (profiles/probe_layouts_dram_N1M-20M_500M.txt)"}
+        roofline["traffic_over_alg"] = round(roofline["traffic"] / alg[dom], 3)
 
     # ---------------- plain vs remapped probe sweep over the skew
     sweep = []
@@ -400,10 +400,18 @@ def run_ours(a, rank, world, local_rank):
             # remapped layout may use a hot prefix (its ids are frequency ranks)
             t_plain, _ = skx.skx_probe_autotune(w.dim, fk_s, w.measure, q, remapped=False)
             t_lay, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=False)
-            t_rem, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True)
+            # the Section III-C model's split threshold for this index (Section IV-B), used as is
+            # and as the seed of the autotuner's split candidates
+            tm64, tm8 = skx.skx_split_threshold(idx, a.width * 4), skx.skx_split_threshold(idx, 8)
+            t_rem, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True, split_hint=tm64)
+            t_model = skx.Tuning()
+            t_model.hot_keys = -1
+            t_model.lane_keys = -1
+            t_model.split_keys = tm64
             variants = {"plain": (w.dim, fk_s, t_plain),
                         "remapped_no_hot_prefix": (dim2, fk2, t_lay),
-                        "remapped": (dim2, fk2, t_rem)}
+                        "remapped": (dim2, fk2, t_rem),
+                        "remapped_split_model_t": (dim2, fk2, t_model)}
             # narrow query copies (Section III-B), same copy for both layouts
             qp = skx.skx_query_prefiltered(q)
             narrow = {}
@@ -413,8 +421,10 @@ def run_ours(a, rank, world, local_rank):
                 narrow[lay] = (c16, q8, keys)
             for lay, (c16, q8, keys) in narrow.items():
                 remapped = lay == "remapped"
-                t16, _ = skx.skx_probe_autotune(c16, keys, w.measure, q, remapped=remapped)
-                t8, _ = skx.skx_probe_autotune(q8, keys, w.measure, qp, remapped=remapped)
+                t16, _ = skx.skx_probe_autotune(c16, keys, w.measure, q, remapped=remapped,
+                                                split_hint=skx.skx_split_threshold(idx, 16) if remapped else 0)
+                t8, _ = skx.skx_probe_autotune(q8, keys, w.measure, qp, remapped=remapped,
+                                               split_hint=tm8 if remapped else 0)
                 variants[f"{lay}_columns16"] = (c16, keys, t16, q)
                 variants[f"{lay}_query8"] = (q8, keys, t8, qp)
             res, times, warm_ms = {}, {}, {}
@@ -450,7 +460,8 @@ def run_ours(a, rank, world, local_rank):
             idx.close()
             same = all(np.array_equal(res["plain"], r) for r in res.values())
             Ds = expected_distinct(a.n, a.f, s)
-            entry = {"zipf_s": s, "results_identical": bool(same), "alg_bytes_per_row": round((8 * a.f + 16 * Ds) / a.f, 3)}
+            entry = {"zipf_s": s, "results_identical": bool(same), "alg_bytes_per_row": round((8 * a.f + 16 * Ds) / a.f, 3),
+                     "split_model_t": {"rows": tm64, "query8": tm8}}
             for name, ms in times.items():
                 med = statistics.median(ms)
                 gather_b = 8 if name.endswith("query8") else 16
@@ -460,7 +471,7 @@ def run_ours(a, rank, world, local_rank):
                                "frac_hbm": round(gbs / peak, 4),
                                "warm_ms": round(statistics.median(warm_ms[name]), 4) if warm_ms.get(name) else None,
                                "tuning": {k: tun.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
-                                                                         "hot_keys", "lane_keys")}}
+                                                                         "hot_keys", "lane_keys", "split_keys")}}
             # other operators on the same column: Q3a top-4000 vs the full Q3 count, Q2 selection
             def t_ms(fn, reps=5):
                 out_ms = []
@@ -495,6 +506,9 @@ def run_ours(a, rank, world, local_rank):
             entry["speedup_query8"] = round(entry["plain_query8"]["ms"] / entry["remapped_query8"]["ms"], 3)
             del narrow
             entry["speedup_layout_only"] = round(entry["plain"]["ms"] / entry["remapped_no_hot_prefix"]["ms"], 3)
+            entry["model_t_vs_autotuned_ms"] = {"model_t": entry["remapped_split_model_t"]["ms"],
+                                                "autotuned": entry["remapped"]["ms"],
+                                                "autotuned_split_keys": int(t_rem.split_keys)}
             sweep.append(entry)
             if s == a.s:
                 probe_lat = times["remapped"]
@@ -509,6 +523,11 @@ def run_ours(a, rank, world, local_rank):
     cache_model = None
     if rank == 0:
         cache_model = predict_l2(a, w, tuning=tuning)
+        cache_model["threshold_t"]["split"] = {
+            "rule": "the model's t (p = 0.5, two thirds of the L2) from the index's fitted counts "
+                    "(skx_split_threshold); the autotuner times t/2, t and 2t",
+            "model_t": t_model, "autotuned_split_keys_query8": int(tuning.split_keys),
+            "autotuned_split_keys_rows64": int(tuning_rows.split_keys)}
 
     # ---------------- batched queries: 512 uneven fact batches in one persistent launch
     batch = None
@@ -578,11 +597,13 @@ def run_ours(a, rank, world, local_rank):
         "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded Zipf, generated on device)",
         "config": config_of(a, world), "impl": "ours",
-        "step": "count -> sort by frequency -> remap fk -> reorder dimension -> probe (filter + GROUP BY SUM)",
+        "step": "count -> sort by frequency -> remap fk -> the query's permuted 8-byte copy of the dimension rows "
+                "(Section III-B) -> probe (filter + GROUP BY SUM)",
         "region_s": round(region_s, 3), "gpu_launches": int(launches),
-        "roofline": roofline, "stages": stage_rep, "alt_step_query_copy": alt_step,
+        "roofline": roofline, "stages": stage_rep, "alt_step_whole_rows": alt_step,
         "probe_tuning": {k: tuning.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll", "hot_keys",
-                                                          "lane_keys")},
+                                                          "lane_keys", "split_keys", "split_bucket")},
+        "split_model_t": t_model,
         "probe": {"remapped_p50_ms": round(statistics.median(probe_lat), 4) if probe_lat else None,
                   "remapped_p99_ms": round(float(np.percentile(probe_lat, 99)), 4) if probe_lat else None,
                   "sweep": sweep},
@@ -739,8 +760,14 @@ def run_cachefit(a):
             skx.skx_reorder(idx2, w.dim, dim3)
             t_fresh = timed(lambda: skx.skx_probe_aggregate(dim3, fks, measure, q, tuning=tr))
             fresh_ok = torch.equal(skx.skx_probe_aggregate(dim3, fks, measure, q, tuning=tr).cpu(), want)
+            # the rebuild decision from a 64M-key sample of the drifted column (Section III-A)
+            t_hot = skx.skx_split_threshold(idx, a.width * 4)
+            pol = skx.skx_index_drift(idx, wd.fk[: 1 << 26], t_hot, max_loss=0.02)
+            pol0 = skx.skx_index_drift(idx, w.fk[: 1 << 26], t_hot, max_loss=0.02)
             rows[-1]["drift"] = {"reshuffled_ranks": 0.1, "stale_probe_ms": t_stale, "fresh_probe_ms": t_fresh,
-                                 "rebuild_ms": t_rebuild, "both_exact": bool(stale_ok and fresh_ok)}
+                                 "rebuild_ms": t_rebuild, "both_exact": bool(stale_ok and fresh_ok),
+                                 "policy_drifted": pol.as_dict(), "policy_undrifted": pol0.as_dict(),
+                                 "rebuild_pays_after_probes": round(t_rebuild / max(1e-9, t_stale - t_fresh), 1)}
             idx2.close()
             del wd, fks, dim3
         idx.close()
@@ -990,7 +1017,9 @@ def run_reference(a, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * total / a.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic (seeded Zipf, host generator)", "config": config_of(a, world),
+            "data": "synthetic (seeded Zipf, host generator)",
+            "config": dict(config_of(a, world), rows_per_step=rows,
+                           sample=f"each step runs the whole path on the first {rows} of the {a.f} fact rows"),
             "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": nthreads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

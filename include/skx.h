@@ -200,6 +200,42 @@ int32_t skx_index_size(const skx_index *idx);                                /* 
  */
 skx_status skx_index_append(skx_index *idx, int32_t n_new, void *stream);
 
+/*
+ * Staleness of an index and the rebuild decision (Section III-A: the index
+ * tolerates changes to the fact column -- results stay exact -- and only
+ * its benefit fades; when to rebuild is a decision made from the data).
+ * The decision looks where the benefit lives: the likely-hit region of
+ * ranks [0, t) (Section IV-B; for example t from skx_split_threshold).
+ *   share_stale  the share of the sampled fact keys whose rank under the
+ *                current index is below t (accesses the layout keeps hot);
+ *   share_fresh  the share held by the sample's own t most frequent ids
+ *                (what a rebuilt index would put below t);
+ *   loss         share_fresh - share_stale: accesses a rebuild would move
+ *                into the hot region;
+ *   rebuild      1 when loss > max_loss.
+ * skx_index_drift takes a device sample of the current fact column in
+ * ORIGINAL ids (d_fk_sample[n]), recodes it through the index and counts it
+ * by rank on `stream` (stream-ordered scratch of 4 (n + N) bytes), copies the
+ * N counts to the host and synchronises `stream`.  Sample keys outside
+ * [0, N) are left out (and reported by skx_stream_status as SKX_EKEYRANGE).
+ * skx_drift_from_counts is its host half, from h_counts_by_rank[N].
+ * Errors: SKX_EINVAL (null pointer, n < 1, t < 1, t > N, max_loss < 0, an
+ * empty sample), SKX_ENOMEM, SKX_ECUDA.
+ */
+typedef struct skx_drift {
+    int64_t sample;      /* sampled keys counted (in [0, N)) */
+    int64_t t;           /* the hot region [0, t) the shares refer to */
+    double share_stale;
+    double share_fresh;
+    double loss;
+    int32_t rebuild;
+    int32_t reserved;
+} skx_drift;
+skx_status skx_index_drift(const skx_index *idx, const int32_t *d_fk_sample, int64_t n, int64_t t, double max_loss,
+                           skx_drift *out, void *stream);
+skx_status skx_drift_from_counts(const uint32_t *h_counts_by_rank, int32_t N, int64_t t, double max_loss,
+                                 skx_drift *out);
+
 /* Frees the index (stream-ordered on the stream it was built on). NULL is a no-op. */
 void skx_index_destroy(skx_index *idx);
 

@@ -92,6 +92,15 @@ class Tuning(ctypes.Structure):
         return f"Tuning({self.as_dict()})"
 
 
+class Drift(ctypes.Structure):
+    _fields_ = [("sample", ctypes.c_int64), ("t", ctypes.c_int64), ("share_stale", ctypes.c_double),
+                ("share_fresh", ctypes.c_double), ("loss", ctypes.c_double), ("rebuild", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("round_rows", ctypes.c_int64),
                 ("memory_budget", ctypes.c_int64), ("timeout_ms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
@@ -157,6 +166,10 @@ def lib():
             L.skx_probe_autotune_ex.restype = st
             L.skx_split_threshold.argtypes = [P, i32, i64, ctypes.c_double, ctypes.POINTER(i64), P]
             L.skx_split_threshold.restype = st
+            L.skx_index_drift.argtypes = [P, P, i64, i64, ctypes.c_double, ctypes.POINTER(Drift), P]
+            L.skx_index_drift.restype = st
+            L.skx_drift_from_counts.argtypes = [P, i32, i64, ctypes.c_double, ctypes.POINTER(Drift)]
+            L.skx_drift_from_counts.restype = st
             L.skx_split_threshold_from_fit.argtypes = [ctypes.c_double, i32, i32, i64, ctypes.c_double,
                                                        ctypes.POINTER(i64)]
             L.skx_split_threshold_from_fit.restype = st
@@ -457,6 +470,25 @@ def skx_probe_autotune(rows, fk, measure, query: Query, remapped: bool = True, o
                                        _dptr(out, "out", torch.int64), _stream(stream), ctypes.byref(t),
                                        ctypes.byref(ms)), "skx_probe_autotune_ex")
     return t, ms.value
+
+
+def skx_index_drift(index: "Index", fk_sample, t: int, max_loss: float = 0.02, stream=None) -> Drift:
+    """Staleness of the index against a device sample of the fact column (original ids)."""
+    import torch
+    d = Drift()
+    _check(lib().skx_index_drift(index._h, _dptr(fk_sample, "fk_sample", torch.int32), fk_sample.numel(), int(t),
+                                 float(max_loss), ctypes.byref(d), _stream(stream)), "skx_index_drift")
+    return d
+
+
+def skx_drift_from_counts(counts_by_rank, t: int, max_loss: float = 0.02) -> Drift:
+    """Host half of skx_index_drift from counts by current rank (numpy, uint32)."""
+    import numpy as np
+    c = np.ascontiguousarray(counts_by_rank, dtype=np.uint32)
+    d = Drift()
+    _check(lib().skx_drift_from_counts(c.ctypes.data_as(ctypes.c_void_p), c.size, int(t), float(max_loss),
+                                       ctypes.byref(d)), "skx_drift_from_counts")
+    return d
 
 
 def skx_probe_resolve_tuning(n: int, row_bytes: int, f: int, query: Query, tuning: Tuning) -> Tuning:

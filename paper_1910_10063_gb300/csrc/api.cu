@@ -10,6 +10,7 @@
 #include <mutex>
 #include <set>
 #include <utility>
+#include <vector>
 
 #include "skx_internal.cuh"
 
@@ -318,6 +319,29 @@ skx_status skx_index_counts_at_ranks(const skx_index *idx, const int64_t *h_rank
     if (d_c) cudaFreeAsync(d_c, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? SKX_OK : cuda_status(e);
+}
+
+skx_status skx_index_drift(const skx_index *idx, const int32_t *d_fk_sample, int64_t n, int64_t t, double max_loss,
+                           skx_drift *out, void *stream) {
+    if (!idx || !d_fk_sample || !out || n < 1 || n >= (int64_t(1) << 32) || t < 1 || t > idx->N ||
+        !(max_loss >= 0.0) || !valid_stream_ptrs(d_fk_sample))
+        return SKX_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ECUDA;
+    int32_t *d_r = nullptr;
+    uint32_t *d_c = nullptr;
+    std::vector<uint32_t> h(size_t(idx->N));
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_r), size_t(n) * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_c), size_t(idx->N) * 4, st);
+    if (e == cudaSuccess) e = launch_remap(idx->rank, idx->N, d_fk_sample, d_r, n, err, st);
+    if (e == cudaSuccess) e = launch_count(d_r, n, idx->N, d_c, err, SKX_COUNT_AUTO, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_c, size_t(idx->N) * 4, cudaMemcpyDeviceToHost, st);
+    if (d_r) cudaFreeAsync(d_r, st);
+    if (d_c) cudaFreeAsync(d_c, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return skx_drift_from_counts(h.data(), idx->N, t, max_loss, out);
 }
 
 void skx_index_destroy(skx_index *idx) {

@@ -137,6 +137,31 @@ skx_status skx_cache_threshold(const double *h_f, int64_t L, int64_t S, double p
     return SKX_OK;
 }
 
+skx_status skx_drift_from_counts(const uint32_t *h_counts_by_rank, int32_t N, int64_t t, double max_loss,
+                                 skx_drift *out) {
+    if (!h_counts_by_rank || !out || N < 1 || t < 1 || t > N || !(max_loss >= 0.0)) return SKX_EINVAL;
+    uint64_t total = 0, stale = 0;
+    for (int32_t r = 0; r < N; ++r) {
+        total += h_counts_by_rank[r];
+        if (r < t) stale += h_counts_by_rank[r];
+    }
+    if (total == 0) return SKX_EINVAL;
+    // the t largest counts: what a rebuilt index would rank below t
+    std::vector<uint32_t> c(h_counts_by_rank, h_counts_by_rank + N);
+    std::nth_element(c.begin(), c.begin() + (t - 1), c.end(), std::greater<uint32_t>());
+    uint64_t fresh = 0;
+    for (int64_t r = 0; r < t; ++r) fresh += c[r];
+    skx_drift d{};
+    d.sample = int64_t(total);
+    d.t = t;
+    d.share_stale = double(stale) / double(total);
+    d.share_fresh = double(fresh) / double(total);
+    d.loss = d.share_fresh - d.share_stale;
+    d.rebuild = d.loss > max_loss ? 1 : 0;
+    *out = d;
+    return SKX_OK;
+}
+
 skx_status skx_powerlaw_fit(const double *h_x, const double *h_y, int64_t n, double *slope, double *intercept) {
     if (!h_x || !h_y || n < 0 || !slope || !intercept) return SKX_EINVAL;
     // centred sums for the least-squares line through (log x, log y)

@@ -126,3 +126,41 @@ def test_model_threshold_is_what_the_probe_resolves():
         assert r.split_keys in (-1, 1000)
         if r.split_keys == 1000:
             assert r.hot_keys < 1000
+
+
+def _drift_case(drift, seed=3, n=20_000, f=400_000):
+    """An index built from one Zipf(1) column and a second column whose popularity drifted: a
+    fraction of the ranks re-shuffled among themselves (0 = the same distribution).  Returns the
+    second column's counts by the first index's ranks, computed by the oracle."""
+    from paper_1910_10063_gb300 import synth
+    w = synth.Workload(n, f, 1.0, seed=seed)
+    _, perm, rank = oracle.build_index(w.fk(), n)
+    r2 = synth.drift_rank_to_id(w.r2id, seed, drift) if drift > 0 else w.r2id
+    w2 = synth.Workload(n, f, 1.0, seed=seed + 1, r2id=r2)
+    by_rank = oracle.histogram(oracle.remap(rank, w2.fk()), n)
+    return by_rank.astype(np.uint32)
+
+
+def test_drift_from_counts_equals_oracle_and_decides():
+    """Section III-A rebuild decision: the shares below t under the stale ranks and under the
+    sample's own order, against a plain restatement over the oracle's counts; an undrifted
+    column keeps the index, a 10 % re-shuffle of the ranks asks for a rebuild."""
+    t = 500
+    for drift, want_rebuild in ((0.0, 0), (0.1, 1)):
+        c = _drift_case(drift)
+        d = skx.skx_drift_from_counts(c, t, max_loss=0.02)
+        total = int(c.astype(np.int64).sum())
+        stale = int(c[:t].astype(np.int64).sum())
+        fresh = int(np.sort(c.astype(np.int64))[::-1][:t].sum())
+        assert d.sample == total and d.t == t
+        assert d.share_stale == stale / total and d.share_fresh == fresh / total
+        assert abs(d.loss - (fresh - stale) / total) < 1e-15
+        assert d.rebuild == want_rebuild, (drift, d.as_dict())
+    # the fresh share is the best any order can do: never below the stale one
+    for t in (1, 10, 19_999, 20_000):
+        d = skx.skx_drift_from_counts(_drift_case(0.1), t)
+        assert d.share_fresh >= d.share_stale and d.loss >= 0
+    with pytest.raises(skx.SkxError):
+        skx.skx_drift_from_counts(np.zeros(10, np.uint32), 3)
+    with pytest.raises(skx.SkxError):
+        skx.skx_drift_from_counts(np.ones(10, np.uint32), 11)
