@@ -404,14 +404,14 @@ def run_ours(a, rank, world, local_rank):
             # and as the seed of the autotuner's split candidates
             tm64, tm8 = skx.skx_split_threshold(idx, a.width * 4), skx.skx_split_threshold(idx, 8)
             t_rem, _ = skx.skx_probe_autotune(dim2, fk2, w.measure, q, remapped=True, split_hint=tm64)
-            t_model = skx.Tuning()
-            t_model.hot_keys = -1
-            t_model.lane_keys = -1
-            t_model.split_keys = tm64
+            tun_model = skx.Tuning()
+            tun_model.hot_keys = -1
+            tun_model.lane_keys = -1
+            tun_model.split_keys = tm64
             variants = {"plain": (w.dim, fk_s, t_plain),
                         "remapped_no_hot_prefix": (dim2, fk2, t_lay),
                         "remapped": (dim2, fk2, t_rem),
-                        "remapped_split_model_t": (dim2, fk2, t_model)}
+                        "remapped_split_model_t": (dim2, fk2, tun_model)}
             # narrow query copies (Section III-B), same copy for both layouts
             qp = skx.skx_query_prefiltered(q)
             narrow = {}

@@ -228,3 +228,23 @@ def test_autotune_with_split_hint_is_exact(data):
     assert np.array_equal(got.cpu().numpy(), want)
     got = skx.skx_probe_aggregate(data["d_dim2"], data["d_fk2"], data["d_m"], q)  # the cached choice
     assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_index_drift_device_equals_host_half():
+    """skx_index_drift (sample recoded and counted on the device) against its host half run on the
+    oracle's counts by rank, on an undrifted and a 10 % drifted column."""
+    n, f = 50_000, 2_000_000
+    w = synth.Workload(n, f, 1.0, seed=12)
+    fk = w.fk()
+    _, perm, rank = oracle.build_index(fk, n)
+    idx = skx.skx_build_index(dev(fk), n)
+    for drift in (0.0, 0.1):
+        r2 = synth.drift_rank_to_id(w.r2id, 12, drift) if drift else w.r2id
+        sample = synth.Workload(n, 1_000_000, 1.0, seed=13, r2id=r2).fk()
+        got = skx.skx_index_drift(idx, dev(sample), 1000, max_loss=0.02)
+        by_rank = oracle.histogram(oracle.remap(rank, sample), n).astype(np.uint32)
+        want = skx.skx_drift_from_counts(by_rank, 1000, max_loss=0.02)
+        assert got.as_dict() == want.as_dict()
+        assert got.rebuild == (1 if drift else 0)
+    assert skx.skx_stream_status() == skx.SKX_OK
+    idx.close()
