@@ -45,7 +45,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--mode", choices=["step", "cachefit", "layouts"], default="step",
+    p.add_argument("--mode", choices=["step", "cachefit", "layouts", "serving"], default="step",
                    help="step: the timed path (default); cachefit: dimension-size sweep with 1B fact rows")
     p.add_argument("--n", type=int, default=20_000_000, help="dimension rows")
     p.add_argument("--f", type=int, default=500_000_000, help="fact rows")
@@ -67,6 +67,7 @@ def parse_args():
     p.add_argument("--serve-n", type=int, default=50_000_000, help="rows of the served dimension table (0 = skip)")
     p.add_argument("--serve-pool", type=int, default=256, help="distinct requests in the serving pool")
     p.add_argument("--serve-requests", type=int, default=512, help="requests per arrival rate")
+    p.add_argument("--serve-repeats", type=int, default=3, help="runs of every serving load point (spread reported)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=0, help="fact rows in the oracle's timed sample (0 = all F)")
     p.add_argument("--ref-rows", type=int, default=50_000_000, help="fact rows per reference-arm step")
@@ -96,6 +97,33 @@ def hbm_peak():
             return float(json.load(fh)["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def pin_to_gpu_local_cpus(dev_index):
+    """Run this process on the CPUs next to the GPU (its PCI function's local_cpulist), so that
+    pinned host buffers allocated afterwards are first touched, and placed, on the GPU's NUMA
+    node and the host threads that copy and poll do not cross sockets.  Returns the CPU list, or
+    None when it cannot be read (nothing is changed then)."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev_index)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as fh:
+            text = fh.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return f"{text} ({bus})"
+    except Exception:
+        return None
 
 
 def expected_distinct(n, f, s):
@@ -219,6 +247,7 @@ def run_ours(a, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    a._local_cpus = pin_to_gpu_local_cpus(local_rank)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -609,6 +638,7 @@ def run_ours(a, rank, world, local_rank):
                   "sweep": sweep},
         "cache_model": cache_model, "batch": batch, "serving": serving,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
+        "host_cpus": a._local_cpus,
     }
     return line
 
@@ -918,14 +948,26 @@ def run_serving(a, dev):
                 "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3), "requests": count}
 
     result = {"table": f"{n // 1_000_000}M x {a.width * 4}B resident rows + resident rank (index from a 25N-row "
-                       f"s=1.0 sample)", "pool_requests": len(pool), "pool_rows": pool_rows}
+                       f"s=1.0 sample)", "pool_requests": len(pool), "pool_rows": pool_rows,
+              "repeats": a.serve_repeats, "host_cpus": getattr(a, "_local_cpus", None)}
+    reps = max(1, a.serve_repeats)
+
+    def spread(xs):
+        return round(max(xs) / min(xs), 3) if min(xs) > 0 else None
+
     for mode, cfg in (("continuous_batching", skx.ServerConfig()),  # library defaults: 128 in flight, 64M-row rounds
                       ("unbatched", skx.ServerConfig(max_inflight=1, round_rows=1 << 40))):
         srv = skx.Server(dim2, rank, cfg)
         run(srv, min(64, len(pool)), None)  # warm-up
-        lat, wall, rows, outs = run(srv, len(pool), None)  # saturation: everything at t = 0
-        cap = len(pool) / wall
-        entry = {"capacity_qps": round(cap, 1), "saturation": summary(lat, wall, rows, len(pool), None), "rates": []}
+        caps, sat = [], []
+        for _ in range(reps):  # saturation: everything at t = 0
+            lat, wall, rows, outs = run(srv, len(pool), None)
+            caps.append(len(pool) / wall)
+            sat.append(summary(lat, wall, rows, len(pool), None))
+        cap = statistics.median(caps)
+        entry = {"capacity_qps": round(cap, 1), "capacity_each": [round(c, 1) for c in caps],
+                 "capacity_spread": spread(caps), "saturation": sat[caps.index(sorted(caps)[len(caps) // 2])],
+                 "rates": []}
         if mode == "continuous_batching":
             ref_outs = outs
             base_cap = cap
@@ -938,8 +980,15 @@ def run_serving(a, dev):
             if mode == "unbatched" and rate > 1.5 * cap:
                 entry["rates"].append({"offered_qps": round(rate, 1), "skipped": "offered load above 1.5x capacity"})
                 continue
-            lat, wall, rows, _ = run(srv, count, rate)
-            entry["rates"].append(dict(summary(lat, wall, rows, count, rate), load_fraction=frac))
+            runs = []
+            for _ in range(reps):
+                lat, wall, rows, _ = run(srv, count, rate)
+                runs.append(summary(lat, wall, rows, count, rate))
+            p50s, p99s = [r["p50_ms"] for r in runs], [r["p99_ms"] for r in runs]
+            med = runs[p99s.index(sorted(p99s)[len(p99s) // 2])]
+            entry["rates"].append(dict(med, load_fraction=frac, p50_each_ms=p50s, p99_each_ms=p99s,
+                                       p99_spread=spread(p99s),
+                                       achieved_qps_each=[r["achieved_qps"] for r in runs]))
         entry["stats"] = srv.stats()
         srv.close()
         result[mode] = entry
@@ -1119,6 +1168,13 @@ def main():
         line = run_cachefit(a) if rank == 0 else None
     elif a.mode == "layouts":
         line = run_layouts(a) if rank == 0 else None
+    elif a.mode == "serving":
+        line = None
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(0)
+            a._local_cpus = pin_to_gpu_local_cpus(0)
+            line = {"mode": "serving", "serving": run_serving(a, torch.device("cuda", 0))}
     else:
         line = run_ours(a, rank, world, local_rank)
     if line is not None:

@@ -544,7 +544,8 @@ typedef struct skx_server_config {
     int64_t round_rows;     /* fact rows per device round, over all requests; default 64 Mi */
     int64_t memory_budget;  /* device arena for admitted requests, bytes; default min(free/2, 16 GiB) */
     int32_t timeout_ms;     /* bound on any internal wait for the device; default 10000 */
-    int32_t reserved0;
+    int32_t cpu_affinity;   /* 0: run the server thread on the CPUs next to the device (read from
+                               sysfs; left alone when they cannot be read); -1: leave it alone */
     skx_tuning tuning;      /* batch kernel tuning (hot_keys 0 = 1024) */
     int32_t reserved[8];
 } skx_server_config;

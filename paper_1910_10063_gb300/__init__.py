@@ -103,7 +103,7 @@ class Drift(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("round_rows", ctypes.c_int64),
-                ("memory_budget", ctypes.c_int64), ("timeout_ms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("timeout_ms", ctypes.c_int32), ("cpu_affinity", ctypes.c_int32),
                 ("tuning", Tuning), ("reserved", ctypes.c_int32 * 8)]
 
 

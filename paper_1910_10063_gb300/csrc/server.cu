@@ -17,9 +17,13 @@
 // their copies overlap with the running rounds: continuous batching.  Every
 // host-side wait polls CUDA events against a deadline; no kernel waits on
 // anything.
+#include <pthread.h>
+#include <sched.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -95,6 +99,43 @@ class Arena {
 };
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// The CPUs next to a device (its PCI function's local_cpulist in sysfs), so
+// that the server thread, which polls the device and copies results, does
+// not run across a socket from it.  Returns false when they cannot be read.
+bool device_local_cpus(int device, cpu_set_t *set) {
+    char bus[64] = {0};
+    if (cudaDeviceGetPCIBusId(bus, sizeof(bus), device) != cudaSuccess) return false;
+    for (char *c = bus; *c; ++c)
+        if (*c >= 'A' && *c <= 'F') *c = char(*c - 'A' + 'a');
+    char path[160];
+    snprintf(path, sizeof(path), "/sys/bus/pci/devices/%s/local_cpulist", bus);
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[4096] = {0};
+    const bool got = fgets(line, sizeof(line), f) != nullptr;
+    fclose(f);
+    if (!got) return false;
+    CPU_ZERO(set);
+    int n = 0;
+    for (char *p = line; *p && *p != '\n';) {
+        char *end = nullptr;
+        const long lo = strtol(p, &end, 10);
+        if (end == p) break;
+        long hi = lo;
+        p = end;
+        if (*p == '-') {
+            hi = strtol(p + 1, &end, 10);
+            p = end;
+        }
+        for (long c = lo; c <= hi && c < CPU_SETSIZE; ++c) {
+            CPU_SET((int)c, set);
+            ++n;
+        }
+        if (*p == ',') ++p;
+    }
+    return n > 0;
+}
 
 }  // namespace
 
@@ -202,6 +243,10 @@ void finish(skx_server *s, Req *q, int state, skx_status st) {
 
 void server_loop(skx_server *s) {
     cudaSetDevice(s->device);
+    if (s->cfg.cpu_affinity == 0) {
+        cpu_set_t set;
+        if (device_local_cpus(s->device, &set)) pthread_setaffinity_np(pthread_self(), sizeof(set), &set);
+    }
     const double wait_limit = s->cfg.timeout_ms / 1e3;
     while (true) {
         std::vector<Req *> to_admit;
@@ -354,7 +399,10 @@ void server_loop(skx_server *s) {
                 progressed = true;
             }
         }
-        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(5));
+        // Nothing moved: the device is busy.  Yield rather than sleep -- a sleep of a few
+        // microseconds lasts the kernel's timer slack (tens of microseconds), which every
+        // request waiting for its round or its copy would pay again.
+        if (!progressed) std::this_thread::yield();
     }
 }
 
