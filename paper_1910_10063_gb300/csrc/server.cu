@@ -189,7 +189,9 @@ void fail_all(skx_server *s, skx_status st) {
     s->cv_done.notify_all();
 }
 
-bool admit_one(skx_server *s, Req *q) {
+// Host bookkeeping of an admission (called with s->mu held): room in the
+// device arena and an in-flight slot.  False when the arena is short.
+bool reserve(skx_server *s, Req *q) {
     // device memory: keys, measures, output
     const size_t fk_b = up256(size_t(q->r.F) * 4), m_b = q->r.h_measure ? fk_b : 0, out_b = up256(size_t(q->nout) * 8);
     const size_t need = fk_b + m_b + out_b;
@@ -205,12 +207,19 @@ bool admit_one(skx_server *s, Req *q) {
     s->free_slots.pop_back();
     q->next_row = 0;
     q->t_admit = seconds(Clock::now());
-    // only copies go on the copy stream: a kernel there would wait for SMs held by a running
-    // round, and every later copy would wait behind it.  The recode C' = Rank(C) and the
-    // cleared output follow on a recode stream once the copy is done.
+    q->state = kCopying;
+    return true;
+}
+
+// The CUDA work of an admission, enqueued without holding s->mu (the lock is
+// what submitters wait for).  Only copies go on the copy stream: a kernel
+// there would wait for SMs held by a running round, and every later copy
+// would wait behind it.  The recode C' = Rank(C) and the cleared output
+// follow on a recode stream once the copy is done.
+void enqueue_admission(skx_server *s, Req *q) {
     unsigned *err = device_error_word();
-    cudaError_t e = cudaSuccess;
-    if (q->r.F > 0) {
+    cudaError_t e = err ? cudaSuccess : cudaErrorInvalidSymbol;
+    if (e == cudaSuccess && q->r.F > 0) {
         e = cudaMemcpyAsync(q->d_fk, q->r.h_fk, size_t(q->r.F) * 4, cudaMemcpyHostToDevice, s->s_copy);
         if (e == cudaSuccess && q->d_m)
             e = cudaMemcpyAsync(q->d_m, q->r.h_measure, size_t(q->r.F) * 4, cudaMemcpyHostToDevice, s->s_copy);
@@ -223,12 +232,10 @@ bool admit_one(skx_server *s, Req *q) {
     if (e == cudaSuccess) e = cudaEventRecord(s->ev_ready[q->slot], s->s_recode);
     if (e != cudaSuccess) {
         cuda_status(e);
-        q->state = kFailed;
+        std::lock_guard<std::mutex> lk(s->mu);
         q->status = SKX_ECUDA;
-        return true;
+        q->state = kFailed;
     }
-    q->state = kCopying;
-    return true;
 }
 
 void finish(skx_server *s, Req *q, int state, skx_status st) {
@@ -258,19 +265,23 @@ void server_loop(skx_server *s) {
             if (s->stop && s->broken) break;
         }
         bool progressed = false;
-        // 1. admission (arrival order; a request waits while memory or slots are short)
+        // 1. admission (arrival order; a request waits while memory or slots are short).  The
+        //    lock covers only host bookkeeping; the copies are enqueued after it is released.
+        std::vector<Req *> admitted;
         {
             std::lock_guard<std::mutex> lk(s->mu);
             while (!s->pending.empty() && !s->free_slots.empty() &&
                    (int32_t)s->active.size() < s->cfg.max_inflight) {
                 Req *q = s->pending.front();
-                if (!admit_one(s, q)) break;
+                if (!reserve(s, q)) break;
                 s->pending.pop_front();
                 s->active.push_back(q);
-                progressed = true;
+                admitted.push_back(q);
             }
             s->max_active = std::max<uint64_t>(s->max_active, s->active.size());
         }
+        for (Req *q : admitted) enqueue_admission(s, q);
+        progressed |= !admitted.empty();
         // 2. a round over every ready request's remaining rows
         std::vector<Req *> last_chunk;
         std::vector<BatchDesc> items;
@@ -366,35 +377,31 @@ void server_loop(skx_server *s) {
             s->round_idx++;
             progressed = true;
         }
-        // 3. completions
+        // 3. completions: the device is polled without the lock; the lock is taken once, only
+        //    when results are ready to hand over
         {
-            std::lock_guard<std::mutex> lk(s->mu);
-            bool any = false;
-            for (auto it = s->active.begin(); it != s->active.end();) {
-                Req *q = *it;
-                bool done = false;
+            std::vector<std::pair<Req *, skx_status>> ended;
+            for (Req *q : s->active) {
                 if (q->state == kFinishing) {
                     const cudaError_t e = cudaEventQuery(s->ev_out[q->slot]);
-                    if (e == cudaSuccess) {
-                        std::memcpy(q->r.h_out, s->h_stage + size_t(q->slot) * kMaxOut, size_t(q->nout) * 8);
-                        finish(s, q, kDone, SKX_OK);
-                        done = true;
-                    } else if (e != cudaErrorNotReady) {
-                        finish(s, q, kFailed, cuda_status(e));
-                        done = true;
-                    }
+                    if (e == cudaSuccess) ended.push_back({q, SKX_OK});
+                    else if (e != cudaErrorNotReady) ended.push_back({q, cuda_status(e)});
                 } else if (q->state == kFailed) {
-                    finish(s, q, kFailed, q->status);
-                    done = true;
-                }
-                if (done) {
-                    it = s->active.erase(it);
-                    any = true;
-                } else {
-                    ++it;
+                    ended.push_back({q, q->status});
                 }
             }
-            if (any) {
+            if (!ended.empty()) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                for (auto &x : ended) {
+                    Req *q = x.first;
+                    if (x.second == SKX_OK) {
+                        std::memcpy(q->r.h_out, s->h_stage + size_t(q->slot) * kMaxOut, size_t(q->nout) * 8);
+                        finish(s, q, kDone, SKX_OK);
+                    } else {
+                        finish(s, q, kFailed, x.second);
+                    }
+                    s->active.erase(std::find(s->active.begin(), s->active.end(), q));
+                }
                 s->cv_done.notify_all();
                 progressed = true;
             }

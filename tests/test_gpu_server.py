@@ -78,13 +78,17 @@ def test_server_replay_poisson(served):
 
 
 def test_server_admission_by_memory(served):
-    # an arena that holds about one mid-size request at a time
+    # an arena that holds about one mid-size request at a time; never more in flight than fit
     big = max(fk.numel() for fk, _, _, _ in served["reqs"])
     cfg = skx.ServerConfig(max_inflight=8, memory_budget=8 * big + (1 << 20))
     srv = skx.Server(served["dim2"], served["rank"], cfg)
     tickets = [srv.submit(fk, m, q) for fk, m, q, _ in served["reqs"]]
     for t, (_, _, _, want) in zip(tickets, served["reqs"]):
         assert np.array_equal(srv.wait(t), want)
+    need = sorted(2 * ((fk.numel() * 4 + 255) // 256 * 256) + (q.nout * 8 + 255) // 256 * 256
+                  for fk, _, q, _ in served["reqs"])
+    fit = int(np.searchsorted(np.cumsum(need), cfg.memory_budget, side="right"))  # the most that fit at once
+    assert 1 <= srv.stats()["max_active"] <= min(fit, cfg.max_inflight)
     # a request that can never fit the arena is refused at submit
     huge = torch.zeros(cfg.memory_budget // 4, dtype=torch.int32)
     with pytest.raises(skx.SkxError) as e:
@@ -94,11 +98,62 @@ def test_server_admission_by_memory(served):
 
 
 def test_server_bounded_wait(served):
+    """A wait of 0 ms right after submitting a 100M-row request cannot see it finished (its keys
+    alone take milliseconds to copy): SKX_ETIMEOUT, deterministically; a patient wait then gets
+    the exact result."""
+    n = served["n"]
+    keys = synth.DeviceWorkload(n, 100_000_000, 1.0, seed=44, width=16, device=DEV, r2id=None,
+                                with_measure=False, with_dim=False).fk
+    fk = torch.empty(keys.numel(), dtype=torch.int32, pin_memory=True)
+    fk.copy_(keys)
+    del keys
     srv = skx.Server(served["dim2"], served["rank"])
-    fk, m, q, want = max(served["reqs"], key=lambda r: r[0].numel())
-    t = srv.submit(fk, m, q)
-    st = skx.lib().skx_server_wait(srv._h, t, 0)  # not finished after 0 ms
-    assert st in (skx.SKX_ETIMEOUT, skx.SKX_OK)
+    t = srv.submit(fk, None, skx.Query.count())
+    assert skx.lib().skx_server_wait(srv._h, t, 0) == skx.SKX_ETIMEOUT
+    want = oracle.probe(served["dim"], fk.numpy(), None, agg=0, filter_col=1, filter_lt=50, group_col=0,
+                        num_groups=1, payload_col=-1, nthreads=16)
     assert np.array_equal(srv.wait(t), want)
     assert skx.lib().skx_server_wait(srv._h, 123456789, 10) == skx.SKX_EINVAL
     srv.close()
+
+
+def test_server_admission_limited_by_the_arena(served):
+    """Six 1M-row requests against an arena that holds two of them: never more than two are in
+    flight, two are, and every result is exact."""
+    n = served["n"]
+    reqs = []
+    for i in range(6):
+        wr = synth.Workload(n, 1_000_000, 1.0, seed=300 + i, width=16)
+        fk = torch.from_numpy(wr.fk()).pin_memory()
+        m = torch.from_numpy(wr.measure()).pin_memory()
+        want = oracle.probe(served["dim"], fk.numpy(), m.numpy(), nthreads=8)
+        reqs.append((fk, m, want))
+    one = 2 * ((1_000_000 * 4 + 255) // 256 * 256) + 4096 * 8  # keys, measures and an output slot
+    cfg = skx.ServerConfig(max_inflight=8, memory_budget=int(2.5 * one))
+    srv = skx.Server(served["dim2"], served["rank"], cfg)
+    tickets = [srv.submit(fk, m, skx.Query.groupby_sum()) for fk, m, _ in reqs]
+    for t, (_, _, want) in zip(tickets, reqs):
+        assert np.array_equal(srv.wait(t), want)
+    st = srv.stats()
+    srv.close()
+    assert st["max_active"] == 2, st
+
+
+def test_server_round_deadline_expires():
+    """A round that outlives the server's bound on waits for the device (timeout_ms = 1) fails its
+    requests with SKX_ETIMEOUT instead of waiting on; the server is then closed cleanly and the
+    device is unaffected.  The rounds are made slow on purpose: 100M uniform keys per round over a
+    20M x 64-byte table (every gather a DRAM miss, about 2 ms a round)."""
+    n = 20_000_000
+    w = synth.DeviceWorkload(n, 300_000_000, 0.0, seed=45, width=16, device=DEV, with_measure=False)
+    fk = torch.empty(w.fk.numel(), dtype=torch.int32, pin_memory=True)
+    fk.copy_(w.fk)
+    cfg = skx.ServerConfig(round_rows=100_000_000, timeout_ms=1)
+    srv = skx.Server(w.dim, None, cfg)  # keys already in table order: no recode
+    t = srv.submit(fk, None, skx.Query.count())
+    st = skx.lib().skx_server_wait(srv._h, t, 60_000)
+    assert st == skx.SKX_ETIMEOUT
+    srv.close()
+    assert skx.skx_stream_status() == skx.SKX_OK
+    del w, fk
+    torch.cuda.empty_cache()
