@@ -284,6 +284,12 @@ skx_status skx_reorder(const skx_index *idx, const void *d_rows_in, void *d_rows
  *
  * The call is layout agnostic: on (plain rows, original keys) and on
  * (skx_reorder'ed rows, skx_remap'ped keys) it returns identical results.
+ *
+ * One exception to the data-error reporting: a row of the hot prefix (keys
+ * below hot_keys) is looked up once per CTA with the sum of its measures, and
+ * not at all when that sum is 0 modulo 2^64 -- so a group key outside
+ * [0, G) on such a row can go unreported.  The result is exact either way
+ * (the row contributes 0).
  * With a remapped layout, rows [0, hot_keys) -- the most popular -- are
  * aggregated per key in shared memory without touching the dimension table
  * until the end of each CTA (threshold-based processing of Section IV-B).
@@ -300,8 +306,8 @@ typedef struct skx_query {
 } skx_query;
 
 /* ------------------------------------------------------------------------
- * Query preprocessing copies (Section III-B: "a copy of the needed dimension
- * table columns for a query, permuted according to the permutation index").
+ * Query preprocessing copies (Section III-B: a query may work on its own
+ * copy of just the dimension columns it needs, laid out in the index's order).
  * idx may be NULL for the identity order (the same narrow copy of the plain
  * layout, so that both layouts can be compared on equal terms).
  *
@@ -372,7 +378,7 @@ skx_status skx_probe_resolve_tuning(int32_t N, int32_t row_bytes, int64_t F, con
 
 /*
  * Autotuner for the probe (threshold-based processing, Section IV-B, picks t
- * "experimentally"): runs skx_probe_aggregate with each candidate launch shape
+ * by measurement): runs skx_probe_aggregate with each candidate launch shape
  * and hot-prefix size on the first min(F, 2^26) rows of the given data,
  * synchronously on `stream`, and returns the fastest in *out (and its time
  * scaled to F in *best_ms if not NULL).  remapped = 0 restricts the search to

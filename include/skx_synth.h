@@ -4,8 +4,8 @@
  * (none of the permutation index's arithmetic) and has a bit-identical host
  * twin in paper_1910_10063_gb300/synth/__init__.py.  The paper has no
  * counterpart beyond its skew model: Zipf frequencies proportional to r^-s
- * over ranks r counted from 1 (Section II-A), keys drawn "in random order"
- * (Section V-A).
+ * over ranks r counted from 1 (Section II-A), with the fact keys drawn
+ * independently and shuffled over the ids (Section V-A).
  *
  * Element i of a stream with key k is x = mix64(k + (i + 1) * 0x9E3779B97F4A7C15),
  * mix64 being the SplitMix64 output function.  All pointers are device

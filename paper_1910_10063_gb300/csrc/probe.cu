@@ -7,8 +7,10 @@
 //  * Persistent grid (a multiple of the SM count); each thread streams the
 //    fk and measure columns with 16-byte loads marked L2 evict-first and keeps
 //    4 x UNROLL rows in flight, issuing all of their dimension gathers before
-//    consuming any of them.  Gathers carry an L2 evict-last policy so the
-//    popular dimension lines survive the fact stream.
+//    consuming any of them.  Gathers carry the L2 eviction priority chosen by
+//    skx_tuning.gather_policy: evict-normal by default (evict-last for the hot
+//    rows, or a split of the priority by rank, measured no faster while the
+//    fact stream is marked evict-first).
 //  * Threshold-based processing (Section IV-B): after remapping, a key k < t
 //    is one of the t most popular rows.  Those rows are not gathered at all
 //    while streaming: the CTA adds the row's measure (or 1 for COUNT) into a
@@ -18,9 +20,11 @@
 //  * The t_lane hottest keys get one shared-memory copy per warp lane, so
 //    the lanes of a warp never collide on the same address -- the paper's
 //    per-SIMD-lane copies of the top values (Section IV-B, aggregation).
-//  * Group sums live in shared memory (int64, one per group) and are merged
-//    into the output with one global atomic per group per CTA: the paper's
-//    hybrid of private buffers for hot data and shared atomics (Section IV-C).
+//  * Group sums live in shared memory (two 32-bit words per group, low and
+//    high, with exact carries: 32-bit shared atomics are native, 64-bit ones
+//    are not) and are merged into the output with one global atomic per group
+//    per CTA: the paper's hybrid of private buffers for hot data and shared
+//    atomics (Section IV-C).
 //    COUNT and SUM accumulate in registers and reduce once per CTA.
 // With t = 0 the same kernel is the plain probe used on the original layout.
 #include "probe_core.cuh"
