@@ -69,6 +69,7 @@ def parse_args():
     p.add_argument("--serve-requests", type=int, default=512, help="requests per arrival rate")
     p.add_argument("--serve-repeats", type=int, default=3, help="runs of every serving load point (spread reported)")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-alt", action="store_true", help="skip the whole-row line (alt_step_whole_rows)")
     p.add_argument("--cpu-rows", type=int, default=0, help="fact rows in the oracle's timed sample (0 = all F)")
     p.add_argument("--ref-rows", type=int, default=50_000_000, help="fact rows per reference-arm step")
     return p.parse_args()
@@ -354,33 +355,35 @@ def run_ours(a, rank, world, local_rank):
     result = out.cpu().numpy().copy()
 
     # ---------------- the same path over whole 64-byte rows
-    for _ in range(a.warmup):
+    alt_step = None
+    for _ in range(0 if a.no_alt else a.warmup):
         flush.zero_()
         step_rows(new_events()).close()
-    evsr = [new_events() for _ in range(a.steps)]
+    evsr = [new_events() for _ in range(0 if a.no_alt else a.steps)]
     keep = []
     torch.cuda.synchronize()
-    for k in range(a.steps):
+    for k in range(len(evsr)):
         flush.zero_()
         keep.append(step_rows(evsr[k]))
     torch.cuda.synchronize()
     for idx in keep:
         idx.close()
-    if not np.array_equal(out.cpu().numpy(), result):
+    if evsr and not np.array_equal(out.cpu().numpy(), result):
         raise RuntimeError("whole-row path disagrees with the query-copy path")
-    msr = sum(e[0].elapsed_time(e[5]) for e in evsr)
-    rows_stage = {s_: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evsr) for i, s_ in enumerate(stages)}
-    Dr = expected_distinct(a.n, a.f, a.s)
-    peak0, _ = hbm_peak()
-    alt_step = {"reorder": "whole 64-byte rows (skx_reorder), probe over them",
-                "value": round(a.f * a.steps / (msr * 1e-3) / 1e9, 3), "unit": UNIT,
-                "ms_per_step": round(msr / a.steps, 4),
-                "stages_ms": {k_: round(v_, 4) for k_, v_ in rows_stage.items()},
-                "probe_alg_bytes": int(8 * a.f + 16 * Dr),
-                "probe_frac": round((8 * a.f + 16 * Dr) / (rows_stage["probe"] * 1e-3) / 1e9 / peak0, 4),
-                "probe_tuning": {k: tuning_rows.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
-                                                                         "hot_keys", "lane_keys", "split_keys")},
-                "split_model_t": t_model["rows64"]}
+    msr = sum(e[0].elapsed_time(e[5]) for e in evsr) if evsr else 0.0
+    if evsr:
+        rows_stage = {s_: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evsr) for i, s_ in enumerate(stages)}
+        Dr = expected_distinct(a.n, a.f, a.s)
+        peak0, _ = hbm_peak()
+        alt_step = {"reorder": "whole 64-byte rows (skx_reorder), probe over them",
+                    "value": round(a.f * a.steps / (msr * 1e-3) / 1e9, 3), "unit": UNIT,
+                    "ms_per_step": round(msr / a.steps, 4),
+                    "stages_ms": {k_: round(v_, 4) for k_, v_ in rows_stage.items()},
+                    "probe_alg_bytes": int(8 * a.f + 16 * Dr),
+                    "probe_frac": round((8 * a.f + 16 * Dr) / (rows_stage["probe"] * 1e-3) / 1e9 / peak0, 4),
+                    "probe_tuning": {k: tuning_rows.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll",
+                                                                             "hot_keys", "lane_keys", "split_keys")},
+                    "split_model_t": t_model["rows64"]}
 
     # ---------------- roofline of the dominant kernel
     peak, peak_src = hbm_peak()
