@@ -135,9 +135,12 @@ def expected_distinct(n, f, s):
     return float(np.sum(-np.expm1(f * np.log1p(-np.minimum(p, 1 - 1e-16)))))
 
 
-def source_sha(path):
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+def source_sha(paths):
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_key, a=None):
@@ -150,7 +153,7 @@ def ncu_traffic(kernel_key, a=None):
         total = 0
         for k in kernel_key.split("+"):
             rec = table[k]
-            if source_sha(os.path.join(ROOT, rec["source"])) != rec["source_sha"]:
+            if source_sha([os.path.join(ROOT, x) for x in rec["sources"]]) != rec["source_sha"]:
                 return None
             if a is not None and rec.get("shape") != [a.n, a.f, a.s, a.width * 4]:
                 return None

@@ -38,11 +38,11 @@ def _shape_args(rec):
 def test_ncu_traffic_lookup(tmp_path, monkeypatch):
     with open(bench.TRAFFIC_PATH) as fh:
         table = json.load(fh)
-    rec = table["k_probe"]
+    rec = table["k_probe/query8"]
     a = _shape_args(rec)
-    # the committed entry is used only while its kernel source is unchanged
-    live = bench.ncu_traffic("k_probe", a)
-    same = bench.source_sha(bench.os.path.join(bench.ROOT, rec["source"])) == rec["source_sha"]
+    # the committed entry is used only while its kernel sources are unchanged
+    live = bench.ncu_traffic("k_probe/query8", a)
+    same = bench.source_sha([bench.os.path.join(bench.ROOT, x) for x in rec["sources"]]) == rec["source_sha"]
     assert live == (rec["bytes_per_launch"] if same else None)
 
     # a private copy: stage sums, shape mismatch, stale source
