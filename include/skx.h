@@ -394,8 +394,10 @@ skx_status skx_probe_autotune(const void *d_rows, int32_t N, int32_t row_bytes, 
  * NULL with hint->split_keys = t_model > 0 (for example from
  * skx_split_threshold): split thresholds t_model / 2, t_model and 2 t_model,
  * each with hot_keys in {off, 2048, 8192} and one or as many CTAs per SM as
- * fit.  Other fields of hint are ignored.  skx_probe_autotune is this call
- * with hint = NULL. */
+ * fit.  Other fields of hint are ignored.  Because the split pays through
+ * cold rows the whole column references several times, the split candidates
+ * and the best unsplit shape are then timed again on the first min(F, 2^28)
+ * rows.  skx_probe_autotune is this call with hint = NULL. */
 skx_status skx_probe_autotune_ex(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
                                  const int32_t *d_measure, int64_t F, const skx_query *q, int remapped,
                                  const skx_tuning *hint, int64_t *d_out, void *stream, skx_tuning *out,

@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "skx_internal.cuh"
@@ -129,18 +130,16 @@ extern "C" skx_status skx_probe_autotune_ex(const void *d_rows, int32_t N, int32
     cudaEvent_t e0, e1;
     SKX_CUDA_TRY(cudaEventCreate(&e0));
     SKX_CUDA_TRY(cudaEventCreate(&e1));
-    float best = 1e30f;
-    skx_tuning best_t{};
-    bool any = false;
-    std::vector<skx_tuning> cand = candidates(remapped, N);
-    if (remapped && hint && hint->split_keys > 0) split_candidates(N, hint->split_keys, cand);
-    for (skx_tuning t : cand) {
-        resolve_probe_tuning(a, t);
+    // best of two runs of candidate t on the first `rows` fact rows (1e30 if it cannot launch)
+    auto time_of = [&](skx_tuning t, int64_t rows) {
+        ProbeArgs b = a;
+        b.F = rows;
+        resolve_probe_tuning(b, t);
         float ms_min = 1e30f;
         bool ok = true;
         for (int rep = 0; rep < 2 && ok; ++rep) {
             cudaEventRecord(e0, st);
-            if (launch_probe(a, t, st) != cudaSuccess) ok = false;
+            if (launch_probe(b, t, st) != cudaSuccess) ok = false;
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
             float ms = 0;
@@ -148,10 +147,35 @@ extern "C" skx_status skx_probe_autotune_ex(const void *d_rows, int32_t N, int32
             ms_min = std::min(ms_min, ms);
         }
         cudaGetLastError();  // a candidate that cannot launch (resources) is skipped
-        if (ok && ms_min < best) {
-            best = ms_min;
-            best_t = t;
+        return std::make_pair(ok ? ms_min : 1e30f, t);
+    };
+    float best = 1e30f;
+    skx_tuning best_t{};
+    bool any = false;
+    for (const skx_tuning &c : candidates(remapped, N)) {
+        const auto r = time_of(c, sample);
+        if (r.first < best) {
+            best = r.first;
+            best_t = r.second;
             any = true;
+        }
+    }
+    // The split pays through cold rows that the whole column references several times, so a
+    // short prefix understates it: its candidates and the best unsplit shape are timed again on
+    // a longer prefix of up to 2^28 rows.
+    std::vector<skx_tuning> sc;
+    if (remapped && hint && hint->split_keys > 0) split_candidates(N, hint->split_keys, sc);
+    int64_t rows_used = sample;
+    if (!sc.empty() && any) {
+        rows_used = std::min<int64_t>(F, int64_t(1) << 28);
+        const auto base = time_of(best_t, rows_used);
+        best = base.first;
+        for (const skx_tuning &c : sc) {
+            const auto r = time_of(c, rows_used);
+            if (r.first < best) {
+                best = r.first;
+                best_t = r.second;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -162,7 +186,7 @@ extern "C" skx_status skx_probe_autotune_ex(const void *d_rows, int32_t N, int32
         g_tune_cache[key_of(N, row_bytes, *q, F, remapped)] = best_t;
     }
     *out = best_t;
-    if (best_ms) *best_ms = best * float(F) / float(sample);
+    if (best_ms) *best_ms = best * float(F) / float(rows_used);
     return SKX_OK;
 }
 
