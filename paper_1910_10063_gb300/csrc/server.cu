@@ -55,6 +55,7 @@ struct Req {
     int slot = -1;
     int64_t next_row = 0;
     int state = kPending;
+    uint64_t round_seq = 0;  // the round whose completion delivers the result (kFinishing)
     skx_status status = SKX_OK;
     double t_submit = 0, t_admit = 0, t_done = 0;
 };
@@ -155,8 +156,11 @@ struct skx_server {
     cudaEvent_t ev_round[2] = {};
     bool round_used[2] = {false, false};
     double round_t0[2] = {0.0, 0.0};  // host time the round was enqueued (for the deadline)
+    uint64_t round_seq_of[2] = {0, 0};  // sequence number of the round in each buffer
+    uint64_t rounds_enqueued = 0, rounds_done = 0;  // rounds are completed in sequence order
+    uint64_t loops = 0;
     int64_t *h_stage = nullptr;  // pinned, kMaxOut per slot
-    std::vector<cudaEvent_t> ev_copied, ev_ready, ev_out;
+    std::vector<cudaEvent_t> ev_copied, ev_ready;
     std::vector<int> free_slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -292,22 +296,37 @@ void server_loop(skx_server *s) {
         // keeps admitting and completing requests instead of waiting (with a deadline)
         const int rb = s->round_idx & 1;
         bool round_free = true;
-        if (s->round_used[rb]) {
-            const cudaError_t qe = cudaEventQuery(s->ev_round[rb]);
-            if (qe == cudaErrorNotReady) {
-                round_free = false;
-                if (seconds(Clock::now()) - s->round_t0[rb] > wait_limit) {
-                    fail_all(s, SKX_ETIMEOUT);
-                    break;
-                }
-            } else if (qe != cudaSuccess) {
+        bool failed = false;
+        // Rounds run in order on the compute stream, so the oldest round in flight is the
+        // only one worth asking about; when it is done, so are the results it carried.
+        for (int k = 0; k < 2 && !failed; ++k) {
+            const int b = (s->round_idx + k) & 1;  // oldest first
+            if (!s->round_used[b] || s->round_seq_of[b] <= s->rounds_done) continue;
+            const cudaError_t qe = cudaEventQuery(s->ev_round[b]);
+            if (qe == cudaSuccess) {
+                s->rounds_done = s->round_seq_of[b];
+                continue;
+            }
+            if (qe != cudaErrorNotReady) {
                 cuda_status(qe);
                 fail_all(s, SKX_ECUDA);
-                break;
+                failed = true;
+            } else if (seconds(Clock::now()) - s->round_t0[b] > wait_limit) {
+                fail_all(s, SKX_ETIMEOUT);
+                failed = true;
             }
+            break;  // a later round cannot be done before this one
         }
+        if (failed) break;
+        if (s->round_used[rb] && s->round_seq_of[rb] > s->rounds_done) round_free = false;
+        // Copies and recodes run in admission order on their streams, so readiness is asked
+        // of the oldest copying request only, and of the next ones while they are ready.
+        bool copies_pending = true;
         for (Req *q : s->active) {
-            if (q->state == kCopying && cudaEventQuery(s->ev_ready[q->slot]) == cudaSuccess) q->state = kReady;
+            if (q->state == kCopying && copies_pending) {
+                if (cudaEventQuery(s->ev_ready[q->slot]) == cudaSuccess) q->state = kReady;
+                else copies_pending = false;
+            }
             if (q->state != kReady || budget <= 0 || !round_free) continue;
             const int64_t take = std::min<int64_t>(q->r.F - q->next_row, budget);
             if (take > 0) {
@@ -359,14 +378,16 @@ void server_loop(skx_server *s) {
                 s->rounds++;
                 for (const BatchDesc &d : items) s->round_rows_total += (uint64_t)d.F;
             }
+            const uint64_t seq = ++s->rounds_enqueued;
             for (Req *q : last_chunk) {
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(s->h_stage + size_t(q->slot) * kMaxOut, q->d_out, size_t(q->nout) * 8,
                                         cudaMemcpyDeviceToHost, s->s_comp);
-                if (e == cudaSuccess) e = cudaEventRecord(s->ev_out[q->slot], s->s_comp);
+                q->round_seq = seq;
                 q->state = kFinishing;
             }
             if (e == cudaSuccess) e = cudaEventRecord(s->ev_round[b], s->s_comp);
+            s->round_seq_of[b] = seq;
             if (e != cudaSuccess) {
                 cuda_status(e);
                 fail_all(s, SKX_ECUDA);
@@ -382,13 +403,8 @@ void server_loop(skx_server *s) {
         {
             std::vector<std::pair<Req *, skx_status>> ended;
             for (Req *q : s->active) {
-                if (q->state == kFinishing) {
-                    const cudaError_t e = cudaEventQuery(s->ev_out[q->slot]);
-                    if (e == cudaSuccess) ended.push_back({q, SKX_OK});
-                    else if (e != cudaErrorNotReady) ended.push_back({q, cuda_status(e)});
-                } else if (q->state == kFailed) {
-                    ended.push_back({q, q->status});
-                }
+                if (q->state == kFinishing && q->round_seq <= s->rounds_done) ended.push_back({q, SKX_OK});
+                else if (q->state == kFailed) ended.push_back({q, q->status});
             }
             if (!ended.empty()) {
                 std::lock_guard<std::mutex> lk(s->mu);
@@ -406,6 +422,7 @@ void server_loop(skx_server *s) {
                 progressed = true;
             }
         }
+        ++s->loops;
         // Nothing moved: the device is busy.  Yield rather than sleep -- a sleep of a few
         // microseconds lasts the kernel's timer slack (tens of microseconds), which every
         // request waiting for its round or its copy would pay again.
@@ -462,11 +479,9 @@ skx_status skx_server_create(const void *d_rows, int32_t N, int32_t row_bytes, c
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_stage, sizeof(int64_t) * kMaxOut * slots);
     s->ev_copied.assign(slots, nullptr);
     s->ev_ready.assign(slots, nullptr);
-    s->ev_out.assign(slots, nullptr);
     for (int i = 0; i < slots && e == cudaSuccess; ++i) {
         e = cudaEventCreateWithFlags(&s->ev_ready[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_copied[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out[i], cudaEventDisableTiming);
         s->free_slots.push_back(slots - 1 - i);
     }
     if (e == cudaSuccess && !device_error_word()) e = cudaErrorMemoryAllocation;
@@ -608,8 +623,6 @@ void skx_server_destroy(skx_server *s) {
     for (cudaEvent_t e : s->ev_ready)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : s->ev_copied)
-        if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : s->ev_out)
         if (e) cudaEventDestroy(e);
     if (s->h_stage) cudaFreeHost(s->h_stage);
     if (s->arena_base) cudaFree(s->arena_base);
