@@ -452,9 +452,9 @@ int orc_cache_hit_rate(const double *f, int64_t L, int64_t S, double *hit, doubl
 }
 
 /* Threshold t of Section IV-B from the Section III-C model: lines are given
- * in transformed-id order, each holding rows_per_line ids; ids below t are
- * "likely cache hits", read as: t covers the leading lines whose modelled hit
- * probability cdf_j is at least p. */
+ * in transformed-id order, each holding rows_per_line ids; ids below t are the
+ * ones expected to hit the cache, read as: t covers the leading lines whose
+ * modelled hit probability cdf_j is at least p. */
 int orc_cache_threshold(const double *f, int64_t L, int64_t S, double p, int32_t rows_per_line, int64_t *t)
 {
     if (!t || rows_per_line < 1 || !(p > 0.0 && p <= 1.0) || L < 1)
