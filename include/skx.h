@@ -356,16 +356,7 @@ typedef struct skx_tuning {
                               about 4 F bytes (deferred rows beyond F/2 are resolved at once). */
     int32_t split_bucket;  /* log2 of the ranks per bucket of the second pass (default 19, range
                               12..26; raised until there are at most 512 buckets) */
-    int32_t cache_rows;    /* rows [0, cache_rows) -- the most popular in a remapped table -- are
-                              copied into each CTA's shared memory (the 8 or 16 bytes the probe
-                              reads) and read from there instead of gathered (Section IV-B's
-                              choice of code path by id, with shared memory as the cache level).
-                              Clamped to what fits beside the group and hot-key sums at
-                              ctas_per_sm CTAs per SM; INT32_MAX asks for as many as fit.
-                              Default (0) and -1: off.  Only for 8-byte rows and rows of a
-                              multiple of 16 bytes whose columns lie in the first 16 bytes;
-                              not with split_keys. */
-    int32_t reserved[6];
+    int32_t reserved[7];
 } skx_tuning;
 
 skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,

@@ -75,8 +75,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("hot_keys", ctypes.c_int32),
                 ("lane_keys", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("gather_policy", ctypes.c_int32), ("split_keys", ctypes.c_int32),
-                ("split_bucket", ctypes.c_int32), ("cache_rows", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("split_bucket", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -35,7 +35,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 int g_sms[kMaxDevices] = {};
 int g_smem_optin[kMaxDevices] = {};
-int g_smem_sm[kMaxDevices] = {};
 thread_local char g_last_cuda[256] = "no CUDA error";
 std::atomic<uint64_t> g_launches{0};
 
@@ -53,9 +52,6 @@ void query_device(int d) {
     v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
     g_smem_optin[d] = v > 0 ? v : 48 * 1024;
-    v = 0;
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, d);
-    g_smem_sm[d] = v > 0 ? v : g_smem_optin[d];
     // keep freed stream-ordered allocations in the device pool between calls
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
@@ -128,13 +124,6 @@ int device_sm_count() {
     std::lock_guard<std::mutex> lk(g_mu);
     query_device(d);
     return g_sms[d];
-}
-
-int device_smem_per_sm() {
-    const int d = current_device();
-    std::lock_guard<std::mutex> lk(g_mu);
-    query_device(d);
-    return g_smem_sm[d];
 }
 
 int device_max_smem_optin() {

@@ -10,7 +10,6 @@
 // wins.  The plain layout (no permutation index) is searched without a hot
 // prefix, because its ids carry no frequency information.
 #include <algorithm>
-#include <climits>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -67,18 +66,16 @@ std::vector<skx_tuning> candidates(int remapped, int32_t N) {
         for (int u : unrolls)
             for (int cps : {0, 1024 / b, 2048 / b}) {
                 if (remapped) {
-                    for (int h : hots_remapped)
-                        for (int cache : {-1, INT32_MAX}) {  // row cache off, or as large as fits
-                            if (h > N) continue;
-                            skx_tuning t{};
-                            t.block_threads = b;
-                            t.unroll = u;
-                            t.ctas_per_sm = cps == 0 ? -1 : cps;
-                            t.hot_keys = h;
-                            t.lane_keys = h == -1 ? -1 : 0;
-                            t.cache_rows = cache;
-                            c.push_back(t);
-                        }
+                    for (int h : hots_remapped) {
+                        if (h > N) continue;
+                        skx_tuning t{};
+                        t.block_threads = b;
+                        t.unroll = u;
+                        t.ctas_per_sm = cps == 0 ? -1 : cps;
+                        t.hot_keys = h;
+                        t.lane_keys = h == -1 ? -1 : 0;
+                        c.push_back(t);
+                    }
                 } else {
                     skx_tuning t{};
                     t.block_threads = b;

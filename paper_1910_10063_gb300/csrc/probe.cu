@@ -27,8 +27,6 @@
 //    atomics (Section IV-C).
 //    COUNT and SUM accumulate in registers and reduce once per CTA.
 // With t = 0 the same kernel is the plain probe used on the original layout.
-#include <algorithm>
-
 #include "probe_core.cuh"
 
 namespace skx {
@@ -49,9 +47,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
     h.lane_lo = reinterpret_cast<uint32_t *>(h.hi + p.t_hot);
     h.lane_hi = reinterpret_cast<int32_t *>(h.lane_lo + (p.t_lane << 5));
     const int nsm = ngrp + p.t_hot + (p.t_lane << 5);  // 8-byte words
-    void *crow = smem + ((nsm + 1) & ~1);               // 16-byte aligned row cache
     for (int i = threadIdx.x; i < nsm; i += blockDim.x) smem[i] = 0;
-    fill_row_cache<PATH>(p, crow);
     __syncthreads();
 
     const uint64_t pol_s = policy_evict_first();
@@ -95,7 +91,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
                 const uint32_t k = (uint32_t)key[j];
                 row[j] = make_int4(0, 0, 0, 0);
                 if (valid[j / 4] && k >= (uint32_t)p.t_hot && k < (uint32_t)p.N)
-                    row[j] = fetch_row_c<PATH, AGG>(p, key[j], pol_g, crow);
+                    row[j] = fetch_row<PATH, AGG>(p, key[j], pol_g);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -120,7 +116,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
                 const int32_t m = AGG == SKX_AGG_COUNT ? 0 : p.measure[idx];
                 int4 row = make_int4(0, 0, 0, 0);
                 if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N)
-                    row = fetch_row_c<PATH, AGG>(p, k, pol_g, crow);
+                    row = fetch_row<PATH, AGG>(p, k, pol_g);
                 handle_row<AGG, PATH, GSMEM>(p, k, m, row, acc, g, h, lane);
             }
         }
@@ -130,8 +126,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
             const int32_t k = ld_stream4(p.fk + i, pol_s);
             const int32_t m = AGG == SKX_AGG_COUNT ? 0 : ld_stream4(p.measure + i, pol_s);
             int4 row = make_int4(0, 0, 0, 0);
-            if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N)
-                row = fetch_row_c<PATH, AGG>(p, k, pol_g, crow);
+            if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N) row = fetch_row<PATH, AGG>(p, k, pol_g);
             handle_row<AGG, PATH, GSMEM>(p, k, m, row, acc, g, h, lane);
         }
     }
@@ -145,7 +140,7 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
             for (int l = 0; l < 32; ++l) s += hot_value(h.lane_lo[(size_t(k) << 5) + l], h.lane_hi[(size_t(k) << 5) + l]);
         }
         if (s == 0) continue;
-        const int4 v = fetch_row_c<PATH, AGG>(p, k, pol_g, crow);
+        const int4 v = fetch_row<PATH, AGG>(p, k, pol_g);
         fold_sum<AGG, GSMEM>(p, v, s, acc, g);
     }
     flush_groups<AGG, GSMEM>(p, acc, g);
@@ -217,7 +212,6 @@ skx_status validate_query(const skx_query *q, int32_t row_bytes) {
 }
 
 void resolve_hot(const ProbeArgs &a, skx_tuning &t, int64_t other_smem);
-void resolve_row_cache(const ProbeArgs &a, skx_tuning &t);
 
 // Fills the defaults of `t` in place.  Idempotent: a resolved tuning resolves
 // to itself ("off" and "as many as fit" are -1, never 0).
@@ -242,28 +236,6 @@ void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t) {
     const int32_t hot = t.hot_keys > 0 ? t.hot_keys : 0;
     if (t.split_keys <= hot || t.split_keys >= a.N) t.split_keys = -1;
     if (t.split_keys > 0) split_buckets(a.N, t.split_keys, &t.split_bucket);
-    resolve_row_cache(a, t);
-}
-
-// The shared-memory row cache gets what the groups and the hot-key sums leave
-// of one CTA's share of the SM (its shared memory over ctas_per_sm, or the
-// per-block limit when the CTA count is left open).
-void resolve_row_cache(const ProbeArgs &a, skx_tuning &t) {
-    const bool c16 = a.row_bytes % 16 == 0 && a.q.filter_col < 4 && a.q.group_col < 4 && a.q.payload_col < 4;
-    const bool c8 = a.row_bytes == 8 && a.q.filter_col < 2 && a.q.group_col < 2 && a.q.payload_col < 2;
-    const int64_t rowsz = c16 ? 16 : (c8 ? 8 : 0);
-    if (t.cache_rows <= 0 || rowsz == 0 || t.split_keys > 0) {
-        t.cache_rows = -1;
-        return;
-    }
-    const bool grp = a.q.agg == SKX_AGG_GROUPBY_SUM;
-    const int64_t gbytes = (grp && a.q.num_groups <= kMaxSmemGroups) ? int64_t(a.q.num_groups) * 8 : 0;
-    const int64_t hot = t.hot_keys > 0 ? int64_t(t.hot_keys) + int64_t(t.lane_keys > 0 ? t.lane_keys : 0) * 32 : 0;
-    int64_t share = device_max_smem_optin();
-    if (t.ctas_per_sm > 0) share = std::min<int64_t>(share, device_smem_per_sm() / t.ctas_per_sm);
-    const int64_t room = (share - 1024 - 16 - gbytes - hot * 8) / rowsz;  // 1 KB reserved per CTA
-    const int64_t rows = std::min<int64_t>(std::min<int64_t>(t.cache_rows, room), a.N);
-    t.cache_rows = rows >= 1 ? (int32_t)rows : -1;
 }
 
 // The hot prefix's shared-memory share: whatever the groups and, for the split
@@ -333,6 +305,7 @@ cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t s
              p.pcol < 2)
         path = kRow8;
     const bool gsmem = a.q.agg == SKX_AGG_GROUPBY_SUM && a.q.num_groups <= kMaxSmemGroups;
+    const size_t smem = size_t((gsmem ? a.q.num_groups : 0) + p.t_hot + p.t_lane * 32) * 8;
 
     const bool vec = af == am;
     if (vec && t.split_keys > 0) {
@@ -340,11 +313,6 @@ cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t s
         e = launch_probe_split(p, a.q.agg, path, gsmem, t, st, &ran);
         if (e != cudaSuccess || ran) return e;
     }
-    // the shared-memory copy of the hottest rows (8 or 16 bytes each), after the group sums and
-    // the hot-key sums, 16-byte aligned
-    p.t_crow = (t.cache_rows > 0 && crow_bytes(path) > 0) ? std::min(t.cache_rows, a.N) : 0;
-    const size_t words = size_t((gsmem ? a.q.num_groups : 0) + p.t_hot + p.t_lane * 32);
-    const size_t smem = ((words + 1) & ~size_t(1)) * 8 + size_t(p.t_crow) * crow_bytes(path);
     switch (a.q.agg) {
         case SKX_AGG_COUNT: return launch_agg<SKX_AGG_COUNT>(p, path, gsmem, t, smem, st, vec);
         case SKX_AGG_SUM: return launch_agg<SKX_AGG_SUM>(p, path, gsmem, t, smem, st, vec);

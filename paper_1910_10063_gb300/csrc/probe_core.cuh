@@ -21,7 +21,6 @@ struct PP {
     int32_t N, row_bytes;
     int32_t fcol, flt, gcol, G, pcol;
     int32_t t_hot, t_lane;
-    int32_t t_crow;  // rows [0, t_crow) are read from the CTA's shared-memory copy
     int32_t gather_policy;
     unsigned long long *out;
     unsigned *err;
@@ -66,49 +65,6 @@ __device__ __forceinline__ int4 fetch_row(const PP &p, int32_t k, uint64_t pol) 
     }
     v.w = 0;
     return v;
-}
-
-// Bytes a row takes in the shared-memory row cache for a row path (0: no cache).
-__host__ __device__ constexpr int crow_bytes(int path) { return path == kRow8 ? 8 : (path == kRow16 ? 16 : 0); }
-
-// The same values as fetch_row, but rows [0, t_crow) -- after remapping, the
-// most popular -- come from the CTA's shared-memory copy of them instead of a
-// gather through L1/L2 (the hot rows' code path of Section IV-B, with shared
-// memory as the cache level the threshold refers to).
-template <int PATH, int AGG>
-__device__ __forceinline__ int4 fetch_row_c(const PP &p, int32_t k, uint64_t pol, const void *cache) {
-    if (PATH == kRowGeneric) return fetch_row<PATH, AGG>(p, k, pol);
-    const bool hit = (uint32_t)k < (uint32_t)p.t_crow;
-    const char *r = p.rows + size_t(k) * size_t(p.row_bytes);
-    int4 v;
-    if (PATH == kRow8) {
-        const int2 raw = hit ? reinterpret_cast<const int2 *>(cache)[k] : ld_gather8(reinterpret_cast<const int2 *>(r), pol);
-        v.x = p.fcol >= 0 ? sel2(raw, p.fcol) : 0;
-        v.y = AGG == SKX_AGG_GROUPBY_SUM ? sel2(raw, p.gcol) : 0;
-        v.z = p.pcol >= 0 ? sel2(raw, p.pcol) : 1;
-    } else {
-        const int4 raw = hit ? reinterpret_cast<const int4 *>(cache)[k] : ld_gather16(reinterpret_cast<const int4 *>(r), pol);
-        v.x = p.fcol >= 0 ? sel4(raw, p.fcol) : 0;
-        v.y = AGG == SKX_AGG_GROUPBY_SUM ? sel4(raw, p.gcol) : 0;
-        v.z = p.pcol >= 0 ? sel4(raw, p.pcol) : 1;
-    }
-    v.w = 0;
-    return v;
-}
-
-// Copies the first crow_bytes(PATH) bytes of rows [0, t_crow) into the CTA's
-// row cache (the caller synchronises afterwards).
-template <int PATH>
-__device__ __forceinline__ void fill_row_cache(const PP &p, void *cache) {
-    if (PATH == kRow8) {
-        int2 *c = reinterpret_cast<int2 *>(cache);
-        for (int i = threadIdx.x; i < p.t_crow; i += blockDim.x)
-            c[i] = *reinterpret_cast<const int2 *>(p.rows + size_t(i) * size_t(p.row_bytes));
-    } else if (PATH == kRow16) {
-        int4 *c = reinterpret_cast<int4 *>(cache);
-        for (int i = threadIdx.x; i < p.t_crow; i += blockDim.x)
-            c[i] = *reinterpret_cast<const int4 *>(p.rows + size_t(i) * size_t(p.row_bytes));
-    }
 }
 
 __device__ __forceinline__ bool passes(const PP &p, const int4 &v) { return p.fcol < 0 || v.x < p.flt; }

@@ -21,7 +21,6 @@ skx_status cuda_status(cudaError_t e);          // records the message, maps to 
 unsigned *device_error_word();                  // the current device's word (a __device__ variable)
 int device_sm_count();                          // SMs of the current device
 int device_max_smem_optin();                    // max dynamic smem per block (opt-in)
-int device_smem_per_sm();                       // shared memory of one SM (all its CTAs)
 void note_launches(int n);                      // adds to the process-wide kernel-launch counter
 // Raises a kernel's dynamic shared-memory limit on the current device, once per (device,
 // kernel): the attribute belongs to each device's context.  dynamic_bytes < 0 asks for the

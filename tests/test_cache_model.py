@@ -164,30 +164,3 @@ def test_drift_from_counts_equals_oracle_and_decides():
         skx.skx_drift_from_counts(np.zeros(10, np.uint32), 3)
     with pytest.raises(skx.SkxError):
         skx.skx_drift_from_counts(np.ones(10, np.uint32), 11)
-
-
-def test_row_cache_resolution():
-    """The probe's shared-memory row cache resolves to what fits beside the group and hot-key sums,
-    and to off where the probe cannot use it (generic rows, the split)."""
-    n = 20_000_000
-    g = skx.Query.groupby_sum(num_groups=1000)
-    q8 = skx.skx_query_prefiltered(g)
-
-    def res(row_bytes, q, **kw):
-        t = skx.Tuning()
-        for k, v in kw.items():
-            setattr(t, k, v)
-        return skx.skx_probe_resolve_tuning(n, row_bytes, 500_000_000, q, t)
-
-    assert res(8, q8).cache_rows == -1                                       # default: off
-    full = res(8, q8, cache_rows=2**31 - 1, ctas_per_sm=2, hot_keys=-1).cache_rows
-    assert full >= 1
-    assert res(8, q8, cache_rows=100, ctas_per_sm=2, hot_keys=-1).cache_rows == 100
-    assert res(8, skx.Query.sum(filter_col=0, payload_col=1), cache_rows=2**31 - 1, ctas_per_sm=2,
-               hot_keys=-1).cache_rows >= full                                # no group sums: more room
-    assert res(64, g, cache_rows=2**31 - 1, ctas_per_sm=2, hot_keys=-1).cache_rows <= full  # 16 bytes a row
-    assert res(12, g, cache_rows=1000).cache_rows == -1                      # generic rows: no cache
-    assert res(64, skx.Query.groupby_sum(filter_col=5), cache_rows=1000).cache_rows == -1
-    with_split = res(8, skx.Query.sum(filter_col=0, payload_col=1), cache_rows=1000, split_keys=50_000, hot_keys=-1)
-    assert with_split.split_keys == 50_000 and with_split.cache_rows == -1   # not with the split
-    assert skx.skx_probe_resolve_tuning(500, 8, 10_000, q8, skx.Tuning(cache_rows=10_000, hot_keys=-1)).cache_rows <= 500

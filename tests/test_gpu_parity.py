@@ -292,8 +292,6 @@ TUNINGS = {
     "hot1_nolane": lambda: _tuning(hot_keys=1, lane_keys=-1),
     "block128_u1": lambda: _tuning(block_threads=128, unroll=1),
     "block256_u4": lambda: _tuning(block_threads=256, unroll=4, hot_keys=3000, lane_keys=32),
-    "row_cache_full": lambda: _tuning(cache_rows=2**31 - 1, hot_keys=-1),
-    "row_cache_hot": lambda: _tuning(cache_rows=5000, hot_keys=64, lane_keys=8, ctas_per_sm=2),
 }
 
 
@@ -368,27 +366,6 @@ def test_probe_many_groups_global_path():
     for t in (skx.Tuning.plain(), None):
         got = skx.skx_probe_aggregate(dev(dim), dev(fk), dev(m), _q(d), tuning=t)
         assert np.array_equal(got.cpu().numpy(), want)
-
-
-@pytest.mark.parametrize("f", [0, 1, 3, 5, 4097, 200_001])
-@pytest.mark.parametrize("off_fk,off_m", [(0, 0), (1, 1), (1, 2)])
-def test_probe_row_cache_paths(probe_data, f, off_fk, off_m):
-    """The shared-memory row cache on the vector path, the unaligned head, the ragged tail and
-    the scalar path (fk and measure at different offsets), over 16-byte, 8-byte and 12-byte rows
-    (the last has no cache: the generic path)."""
-    fk, m = probe_data["fk2"][:f], probe_data["m"][:f]
-    d_fk, d_m = offset_view(fk, off_fk), offset_view(m, off_m)
-    for width, cols in ((16, None), (2, [0, 2]), (3, [0, 1, 2])):
-        rows = probe_data["dim2"] if cols is None else np.ascontiguousarray(probe_data["dim2"][:, cols])
-        d = dict(QUERIES["groupby"]) if width != 2 else dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=-1,
-                                                                filter_lt=0, group_col=0, num_groups=1000,
-                                                                payload_col=1)
-        want = _oracle(rows, fk, m, d)
-        d_rows = probe_data["d_dim2"] if cols is None else dev(rows)
-        for t in (_tuning(cache_rows=2**31 - 1, hot_keys=-1), _tuning(cache_rows=777, hot_keys=100, lane_keys=4)):
-            got = skx.skx_probe_aggregate(d_rows, d_fk, d_m, _q(d), tuning=t)
-            assert np.array_equal(got.cpu().numpy(), want), (f, off_fk, off_m, width)
-    assert status() == skx.SKX_OK
 
 
 @pytest.mark.parametrize("off_fk,off_m", [(1, 1), (3, 3), (1, 2), (0, 3)])
