@@ -171,18 +171,25 @@ EFFECTIVE_L2_BYTES = 88_000_000
 
 
 def count_kernels(fk, n, f, method="auto"):
-    """Kernels the library's automatic count runs on this column: it samples 8192 keys at stride
-    f // 8192 on the device and takes the partitioned count (2^24 <= n <= 2^28, f >= 2^28) unless
-    60 % or more of the sampled keys repeat in the sample.  The same rule, evaluated here, only
-    labels the stage in the report."""
+    """Kernels the library's count runs on this column; the same rule as the library's, evaluated
+    here, only labels the stage in the report.  The automatic count (2^16 <= n <= 2^28,
+    f >= 2^26) samples 8192 keys at stride f // 8192 on the device and takes the partitioned count
+    unless the share d of valid sampled keys whose id repeats in the sample is 85 % or more, or
+    60-85 % with n < 2^24, or 70-85 % in the exact layout.  The partitioned count sizes its buckets
+    from a sample (k_part_sample, k_part_plan) up to 1024 buckets of 2^15 ids, with a pre-count
+    pass beyond."""
+    sampled = (n + 32767) // 32768 <= 1024 and f >= 65536 and 3 * f < 2 ** 32
+    part = ("k_part_sample+k_part_plan" if sampled else "k_part_count") + "+k_part_scatter+k_part_hist"
     if method != "auto":
-        return "k_histogram" if method == "single" else "k_part_count+k_part_scatter+k_part_hist"
-    if not (2 ** 24 <= n <= 2 ** 28 and f >= 2 ** 28):
+        return "k_histogram" if method == "single" else part
+    if not (2 ** 16 <= n <= 2 ** 28 and f >= 2 ** 26):
         return "k_histogram"
     sample = fk[:: f // 8192][:8192].cpu().numpy()
+    sample = sample[(sample >= 0) & (sample < n)]
     _, c = np.unique(sample, return_counts=True)
     dup = float(c[c >= 2].sum()) / max(sample.size, 1)
-    return "k_histogram" if dup >= 0.6 else "k_part_count+k_part_scatter+k_part_hist"
+    mid = n >= 2 ** 24 and (sampled or dup < 0.70)
+    return part if dup < 0.85 and (dup < 0.60 or mid) else "k_histogram"
 
 
 class ClockSampler:

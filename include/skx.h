@@ -123,19 +123,25 @@ skx_status skx_build_index_from_counts(const uint32_t *d_counts, int32_t N, int6
  *                          partitioned count's scratch can be allocated) a
  *                          kernel samples 8192 keys of d_fk and picks on the
  *                          device, without a host synchronisation: the single
- *                          pass when 60 % or more of the sampled keys repeat
+ *                          pass when 85 % or more of the sampled keys repeat
  *                          in the sample (heavy skew), the partitioned count
- *                          when fewer than 25 % do, and in between the
- *                          partitioned count from N >= 2^22 ids.  Smaller
+ *                          when fewer than 60 % do, and in between the
+ *                          partitioned count from N >= 2^24 ids (above 2^25
+ *                          ids only while fewer than 70 % repeat).  Smaller
  *                          inputs take the single pass;
  *   SKX_COUNT_SINGLE_PASS  one pass over d_fk, a per-CTA shared-memory cache
  *                          of hot ids and L2 atomics for the rest;
  *   SKX_COUNT_PARTITIONED  radix partition of the keys by 2^15-id buckets
- *                          (two passes over d_fk, 2 bytes per key of scratch
- *                          written and read back) and a shared-memory count
- *                          per bucket; no random global access.  Needs
- *                          N <= 2^28; allocates 2 * F bytes (plus a few MB)
- *                          of stream-ordered scratch.
+ *                          (2 bytes per key of scratch written and read back)
+ *                          and a shared-memory count per bucket; no random
+ *                          global access.  Up to 2^25 ids (1024 buckets) and
+ *                          for 65536 <= F < 2^32 / 3 the bucket regions are
+ *                          sized from a sample of 65536 keys and d_fk is read
+ *                          once; otherwise, or when a bucket outgrows its
+ *                          sampled region, an exact pre-count pass sizes them
+ *                          (d_fk read twice).  Needs N <= 2^28; allocates
+ *                          4 * F bytes of stream-ordered scratch with sampled
+ *                          regions, 2 * F bytes otherwise (plus a few MB).
  * Errors: as skx_count; SKX_EINVAL for an unknown method; SKX_ENOTSUP when
  * SKX_COUNT_PARTITIONED is asked for with N > 2^28.
  */

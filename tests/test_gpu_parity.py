@@ -120,12 +120,14 @@ def test_count_methods_parity(method, n, f, s, seed, offset):
 
 
 @pytest.mark.parametrize("n,f,s", [
-    (1 << 24, (1 << 28) + 5, 1.0),        # mid skew, many ids: partitioned
-    (1 << 24, (1 << 28) + 5, 1.5),        # heavy skew: the single pass
+    (1 << 24, (1 << 28) + 5, 1.0),        # about 45 % of the sampled keys repeat: partitioned
+    (1 << 24, (1 << 28) + 5, 1.5),        # heavy skew (95 %): the single pass
     (1 << 16, (1 << 26) + 3, 0.0),        # the fewest sampled ids, flat: partitioned (2 buckets)
     ((1 << 20) + 7, (1 << 26) + 3, 0.0),  # flat: partitioned
-    ((1 << 20) + 7, (1 << 26) + 3, 1.0),  # mid skew below 2^22 ids: the single pass
-    ((1 << 22) + 1, (1 << 26) + 9, 1.0),  # mid skew from 2^22 ids: partitioned
+    ((1 << 20) + 7, (1 << 26) + 3, 1.2),  # 60-85 % repeat, below 2^24 ids: the single pass
+    ((1 << 24) + 3, (1 << 26) + 9, 1.2),  # 60-85 % repeat, from 2^24 ids, sampled layout: partitioned
+    ((1 << 25) + 5, (1 << 26) + 3, 1.1),  # 60-70 % repeat, exact layout (1025 buckets): partitioned
+    ((1 << 25) + 5, (1 << 26) + 3, 1.2),  # 70-85 % repeat, exact layout: the single pass
 ])
 def test_count_auto_choice_parity(n, f, s):
     """Sizes where the automatic count samples the column and picks an
@@ -175,6 +177,39 @@ def test_count_methods_key_range(method):
     keep = np.ones(bad.size, dtype=bool)
     keep[[0, 12345, 500_000]] = False
     assert np.array_equal(_counts_np(c), oracle.histogram(bad[keep], n))
+
+
+@pytest.mark.parametrize("offset", [0, 3])
+def test_count_sampled_layout_fallbacks(offset):
+    """The partitioned count sizes its bucket regions from 65536 keys at an even stride.
+    - Every 4th key (exactly the sampled ones) is one id: the sample sees one bucket, the
+      others outgrow their regions in the partition pass, and the exact layout recounts.
+    - 90 % of the keys out of range over 1024 buckets: too few valid samples for the regions
+      to fit, so the exact layout runs from the start (and the range error is reported).
+    - N = 2^25 (1024 buckets) is the largest sampled layout, 2^25 + 5 the smallest exact one."""
+    rng = np.random.default_rng(31 + offset)
+    n = 1 << 20
+    fk = rng.integers(0, n, 65536 * 4).astype(np.int32)
+    fk[::4] = 5  # the sampled positions: stride F / 65536 = 4
+    c = skx.skx_count_ex(offset_view(fk, offset), n, skx.SKX_COUNT_PARTITIONED)
+    assert status() == skx.SKX_OK
+    assert np.array_equal(_counts_np(c), oracle.histogram(fk, n))
+
+    n = 1 << 25
+    bad = rng.integers(0, n, 65536 * 8).astype(np.int32)
+    out = rng.random(bad.size) < 0.9
+    bad[out] = -3
+    c = skx.skx_count_ex(offset_view(bad, offset), n, skx.SKX_COUNT_PARTITIONED)
+    assert status() == skx.SKX_EKEYRANGE
+    assert np.array_equal(_counts_np(c), oracle.histogram(bad[~out], n))
+
+    for n in (1 << 25, (1 << 25) + 5):
+        fk = synth.Workload(n, 2_000_003, 1.0, seed=9).fk()
+        c = skx.skx_count_ex(offset_view(fk, offset), n, skx.SKX_COUNT_PARTITIONED)
+        assert status() == skx.SKX_OK
+        assert np.array_equal(_counts_np(c), oracle.histogram(fk, n))
+        del c
+    torch.cuda.empty_cache()
 
 
 def test_count_method_errors():
