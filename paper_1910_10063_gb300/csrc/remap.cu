@@ -18,6 +18,7 @@ namespace skx {
 namespace {
 
 constexpr int kRemapBlock = 512;
+constexpr int kQueryRows = 4;  // rows per thread per step of the query copy
 constexpr int kRemapUnroll = 2;
 
 __device__ __forceinline__ int32_t remap_one(int32_t k, const int32_t *__restrict__ rank, int32_t N, unsigned *err) {
@@ -229,21 +230,56 @@ __global__ void __launch_bounds__(512)
 // Query-specific copy (Sections I and III-B): the predicate is evaluated once per
 // dimension row, as for the Q2 bitmap, and folded into the copy:
 // out[r] = {passes ? group : sentinel, payload}.
+// Each thread takes U rows per step (grid stride) and issues all of their perm
+// loads, then all of their row loads, before it writes any, so U rows' latencies
+// overlap.  VEC: the used columns lie in one aligned 16-byte chunk of a 16-byte
+// aligned row (chunk index `chunk`), read with one load.
+__device__ __forceinline__ int32_t pick4(const int4 &c, int i) {
+    return i == 0 ? c.x : (i == 1 ? c.y : (i == 2 ? c.z : c.w));
+}
+
+template <int U, bool VEC>
 __global__ void __launch_bounds__(512)
     k_reorder_query(const int32_t *__restrict__ perm, int32_t N, const int32_t *__restrict__ in, int32_t words,
-                    int32_t fcol, int32_t flt, int32_t gcol, int32_t pcol, int32_t sentinel,
+                    int32_t fcol, int32_t flt, int32_t gcol, int32_t pcol, int32_t sentinel, int32_t chunk,
                     int2 *__restrict__ out) {
     const bool wide = words >= 16;  // rows of 64 bytes or more: fetch 64 bytes per miss
-    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < N; r += int64_t(gridDim.x) * blockDim.x) {
-        const int32_t src = perm ? __ldg(perm + r) : (int32_t)r;
-        if ((uint32_t)src >= (uint32_t)N) continue;
-        const int32_t *row = in + int64_t(src) * words;
-        auto rd = [wide](const int32_t *q) { return wide ? ld_row4_p64(q) : __ldg(q); };
-        const bool pass = fcol < 0 || rd(row + fcol) < flt;
-        int2 v;
-        v.x = pass ? (gcol >= 0 ? rd(row + gcol) : 0) : sentinel;
-        v.y = pcol >= 0 ? rd(row + pcol) : 1;
-        out[r] = v;
+    const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t r0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r0 < N; r0 += nthr * U) {
+        int32_t src[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = r0 + u * nthr;
+            src[u] = r < N ? (perm ? __ldg(perm + r) : (int32_t)r) : -1;
+        }
+        int32_t fv[U], gv[U], pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            fv[u] = 0;
+            gv[u] = 0;
+            pv[u] = 1;
+            if ((uint32_t)src[u] >= (uint32_t)N) continue;
+            const int32_t *row = in + int64_t(src[u]) * words;
+            if (VEC) {
+                const int4 *q = reinterpret_cast<const int4 *>(row) + chunk;
+                const int4 c = wide ? ld_row16_p64(q) : __ldg(q);
+                if (fcol >= 0) fv[u] = pick4(c, fcol & 3);
+                if (gcol >= 0) gv[u] = pick4(c, gcol & 3);
+                if (pcol >= 0) pv[u] = pick4(c, pcol & 3);
+            } else {
+                auto rd = [wide](const int32_t *a) { return wide ? ld_row4_p64(a) : __ldg(a); };
+                if (fcol >= 0) fv[u] = rd(row + fcol);
+                if (gcol >= 0) gv[u] = rd(row + gcol);
+                if (pcol >= 0) pv[u] = rd(row + pcol);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = r0 + u * nthr;
+            if (r >= N || (uint32_t)src[u] >= (uint32_t)N) continue;
+            const bool pass = fcol < 0 || fv[u] < flt;
+            out[r] = make_int2(pass ? gv[u] : sentinel, pv[u]);
+        }
     }
 }
 
@@ -322,9 +358,27 @@ cudaError_t launch_reorder_query(const int32_t *d_perm, int32_t N, const void *d
     if (N <= 0) return cudaSuccess;
     const bool grp = q.agg == SKX_AGG_GROUPBY_SUM;
     const int32_t sentinel = grp ? q.num_groups : 1;
-    k_reorder_query<<<grid_for(N, 512, 4), 512, 0, st>>>(
-        d_perm, N, static_cast<const int32_t *>(d_in), row_bytes / 4, q.filter_col, q.filter_lt,
-        grp ? q.group_col : -1, q.agg == SKX_AGG_COUNT ? -1 : q.payload_col, sentinel, static_cast<int2 *>(d_out));
+    const int32_t words = row_bytes / 4, fcol = q.filter_col, gcol = grp ? q.group_col : -1,
+                  pcol = q.agg == SKX_AGG_COUNT ? -1 : q.payload_col;
+    // one 16-byte load per row when every used column is in the same aligned chunk
+    int32_t chunk = -1;
+    bool vec = words % 4 == 0 && aligned16(d_in);
+    for (int32_t c : {fcol, gcol, pcol}) {
+        if (c < 0) continue;
+        if (chunk < 0) chunk = c / 4;
+        vec = vec && c / 4 == chunk;
+    }
+    if (chunk < 0) chunk = 0;
+    const int32_t *in = static_cast<const int32_t *>(d_in);
+    int2 *out = static_cast<int2 *>(d_out);
+    // 29 registers (VEC) leave room for four 512-thread CTAs per SM, 43 for two
+    const int grid = grid_for((N + kQueryRows - 1) / kQueryRows, 512, vec ? 4 : 2);
+    if (vec)
+        k_reorder_query<kQueryRows, true><<<grid, 512, 0, st>>>(d_perm, N, in, words, fcol, q.filter_lt, gcol, pcol,
+                                                                sentinel, chunk, out);
+    else
+        k_reorder_query<kQueryRows, false><<<grid, 512, 0, st>>>(d_perm, N, in, words, fcol, q.filter_lt, gcol,
+                                                                 pcol, sentinel, chunk, out);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -130,6 +130,14 @@ __device__ __forceinline__ int ld_row4_p64(const int *p) {
     asm volatile("ld.global.nc.L2::64B.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
+// The same for an aligned 16-byte chunk of a row.
+__device__ __forceinline__ int4 ld_row16_p64(const int4 *p) {
+    int4 v;
+    asm volatile("ld.global.nc.L2::64B.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
 
 __device__ __forceinline__ void raise_error(unsigned *err, unsigned bit) {
     if (err) atomicOr(err, bit);

@@ -38,7 +38,6 @@ constexpr int kTile = kSortBlock * kRounds;  // 4096 keys per tile
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kSortBlock * kScanItems;  // 4096
 
-__device__ __forceinline__ uint32_t first_key(const uint32_t *cnt, uint32_t i) { return ~cnt[i]; }
 
 // Key sources of a pass.
 enum KeySrc {
@@ -81,13 +80,13 @@ __global__ void __launch_bounds__(kSortBlock)
                     const uint32_t *__restrict__ vals_in, uint32_t n_host, const uint32_t *__restrict__ n_dev,
                     int shift, uint32_t *__restrict__ tile_hist, uint32_t num_tiles, uint32_t cmax,
                     unsigned *err) {
-    __shared__ uint32_t s_cnt[kWarps][kBins];
+    __shared__ uint32_t s_hist[kBins];  // the tile's digit counts (no order needed here)
     const uint32_t n = n_dev ? *n_dev : n_host;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     // a length read from the device that exceeds the grid (more heavy ids than the
     // bound F / 255 allows) would leave ids unsorted: report it
     if (n_dev && blockIdx.x == 0 && threadIdx.x == 0 && n > gridDim.x * kTile) raise_error(err, kErrCountBound);
-    for (int i = threadIdx.x; i < kWarps * kBins; i += kSortBlock) (&s_cnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kBins; i += kSortBlock) s_hist[i] = 0;
     __syncthreads();
     const uint32_t tile = blockIdx.x;
     const uint32_t base = tile * kTile + warp * (32 * kRounds);
@@ -113,16 +112,11 @@ __global__ void __launch_bounds__(kSortBlock)
         for (int r = 0; r < kRounds; ++r) {
             const uint32_t d = dig[r];
             const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (d < (uint32_t)kBins && lane == (unsigned)(__ffs(peers) - 1)) s_cnt[warp][d] += __popc(peers);
+            if (d < (uint32_t)kBins && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(s_hist + d, __popc(peers));
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kBins; d += kSortBlock) {
-        uint32_t s = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += s_cnt[w][d];
-        tile_hist[(size_t)d * num_tiles + tile] = s;
-    }
+    for (int d = threadIdx.x; d < kBins; d += kSortBlock) tile_hist[(size_t)d * num_tiles + tile] = s_hist[d];
 }
 
 // ------------------------------------------------------------------ scan

@@ -475,6 +475,36 @@ def test_query_copy_end_to_end(probe_data, qname):
     assert np.array_equal(got[:, 0], key) and np.array_equal(got[:, 1], pay)
 
 
+@pytest.mark.parametrize("width,offset", [(3, 0), (4, 0), (4, 1), (5, 0), (8, 2), (16, 0), (16, 3)])
+def test_query_copy_layouts(width, offset):
+    """The query copy over rows of 12 to 64 bytes, 16-byte aligned and not, with the used columns
+    in one aligned 16-byte chunk (one vector load per row) or spread over several, and N not a
+    multiple of the rows one grid step covers: element by element against the oracle's permuted
+    rows, in both orders (the index's and the identity)."""
+    rng = np.random.default_rng(40 + width + offset)
+    n = 70_001
+    dim = rng.integers(-50, 150, (n, width)).astype(np.int32)
+    fk = rng.integers(0, n, 300_007).astype(np.int32)
+    idx = skx.skx_build_index(dev(fk), n)
+    _, perm, _ = oracle.build_index(fk, n)
+    buf = torch.zeros(n * width + offset + 8, dtype=torch.int32, device=DEV)
+    rows = buf[offset:offset + n * width].view(n, width)
+    rows.copy_(torch.from_numpy(dim))
+    cases = [(1, 0, 2), (width - 1, 0, width - 1), (-1, width // 2, 0), (2, width - 1, 1)]
+    for index, src in ((idx, oracle.reorder(perm, dim)), (None, dim)):
+        for fcol, gcol, pcol in cases:
+            for agg, ng in ((oracle.AGG_GROUPBY_SUM, 160), (oracle.AGG_SUM, 1), (oracle.AGG_COUNT, 1)):
+                q = skx.Query(agg, fcol, 40, gcol, ng, pcol)
+                got = skx.skx_reorder_query(index, rows, q).cpu().numpy()
+                passes = src[:, fcol] < 40 if fcol >= 0 else np.ones(n, bool)
+                key = src[:, gcol] if agg == oracle.AGG_GROUPBY_SUM else np.zeros(n, np.int32)
+                key = np.where(passes, key, ng if agg == oracle.AGG_GROUPBY_SUM else 1)
+                pay = src[:, pcol] if agg != oracle.AGG_COUNT else np.ones(n, np.int32)
+                assert np.array_equal(got[:, 0], key), (fcol, gcol, pcol, agg)
+                assert np.array_equal(got[:, 1], pay), (fcol, gcol, pcol, agg)
+    assert status() == skx.SKX_OK
+
+
 # ------------------------------------------------------------------ Q3a, Q2, maintenance
 @pytest.mark.parametrize("k", [1, 31, 32, 33, 4000, 60_000])
 def test_topk_counts_parity(probe_data, k):
