@@ -146,6 +146,98 @@ __global__ void __launch_bounds__(512) k_probe(PP p) {
     flush_groups<AGG, GSMEM>(p, acc, g);
 }
 
+// The probe over 8-byte rows without a hot prefix -- the query's permuted copy
+// of Section III-B, the timed path -- as k_probe<AGG, kRow8, GSMEM, 1> computes
+// it with t = 0 and the default gather priority, in a leaner kernel: no
+// hot-prefix state, the rows kept as 8-byte pairs, 32-bit loop indices.  At
+// most 40 registers (against 54) let three 512-thread CTAs share an SM instead
+// of two, so half as many gathers again are in flight.
+template <int AGG, bool GSMEM>
+__global__ void __launch_bounds__(512, 3) k_probe_r8(PP p) {
+    extern __shared__ unsigned long long smem[];
+    GrpRef g;
+    g.lo = reinterpret_cast<uint32_t *>(smem);
+    g.hi = g.lo + (GSMEM ? p.G : 0);
+    if (GSMEM)
+        for (int i = threadIdx.x; i < p.G; i += blockDim.x) smem[i] = 0;
+    __syncthreads();
+    const uint64_t pol_s = policy_evict_first();
+    unsigned long long acc = 0;
+    const int2 *rows = reinterpret_cast<const int2 *>(p.rows);
+    const int4 *fk4 = reinterpret_cast<const int4 *>(p.fk + p.head);
+    const int4 *m4 = reinterpret_cast<const int4 *>((AGG == SKX_AGG_COUNT ? p.fk : p.measure) + p.head);
+    // F < 2^32, so the vector count and indices fit 32 bits
+    const uint32_t nvec = (uint32_t)((p.F - p.head) >> 2);
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nthr = gridDim.x * blockDim.x;
+    // the row's filter, group and payload values from the pair (columns 0 or 1)
+    auto unpack = [&p](const int2 &r) {
+        int4 v;
+        v.x = p.fcol >= 0 ? sel2(r, p.fcol) : 0;
+        v.y = AGG == SKX_AGG_GROUPBY_SUM ? sel2(r, p.gcol) : 0;
+        v.z = p.pcol >= 0 ? sel2(r, p.pcol) : 1;
+        v.w = 0;
+        return v;
+    };
+    int4 nk = make_int4(0, 0, 0, 0), nm = nk;
+    if (tid < nvec) {
+        nk = ld_stream16(fk4 + tid, pol_s);
+        if (AGG != SKX_AGG_COUNT) nm = ld_stream16(m4 + tid, pol_s);
+    }
+    for (uint32_t i = tid; i < nvec; i += nthr) {
+        const int32_t key[4] = {nk.x, nk.y, nk.z, nk.w};
+        const int32_t mea[4] = {nm.x, nm.y, nm.z, nm.w};
+        int2 r[4];
+        bool use[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            use[j] = (uint32_t)key[j] < (uint32_t)p.N;
+            r[j] = use[j] ? __ldg(rows + key[j]) : make_int2(0, 0);
+        }
+        // the next vectors are in flight while these gathers resolve
+        if (nvec - i > nthr) {
+            nk = ld_stream16(fk4 + (i + nthr), pol_s);
+            if (AGG != SKX_AGG_COUNT) nm = ld_stream16(m4 + (i + nthr), pol_s);
+        }
+        if (!(use[0] && use[1] && use[2] && use[3])) raise_error(p.err, kErrKeyRange);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (use[j]) fold_row<AGG, GSMEM>(p, unpack(r[j]), mea[j], acc, g);
+    }
+    // unaligned head (< 4 rows) and ragged tail (< 4 rows)
+    if (tid < 8) {
+        const int64_t tail0 = p.head + (int64_t(nvec) << 2);
+        int64_t idx = -1;
+        if (tid < p.head) idx = tid;
+        else if (tid >= 4 && tail0 + (tid - 4) < p.F) idx = tail0 + (tid - 4);
+        if (idx >= 0) {
+            const int32_t k = p.fk[idx];
+            const int32_t m = AGG == SKX_AGG_COUNT ? 0 : p.measure[idx];
+            if ((uint32_t)k < (uint32_t)p.N) fold_row<AGG, GSMEM>(p, unpack(__ldg(rows + k)), m, acc, g);
+            else raise_error(p.err, kErrKeyRange);
+        }
+    }
+    flush_groups<AGG, GSMEM>(p, acc, g);
+}
+
+template <int AGG, bool GSMEM>
+cudaError_t launch_r8(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st) {
+    auto kern = k_probe_r8<AGG, GSMEM>;
+    cudaError_t e = set_smem_limit_once(reinterpret_cast<const void *>(kern), -1);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t.block_threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (t.ctas_per_sm > 0 && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;
+    const int64_t need = (((p.F - p.head) >> 2) + t.block_threads - 1) / t.block_threads;
+    int64_t grid = int64_t(device_sm_count()) * per_sm;
+    if (need < grid) grid = need < 1 ? 1 : need;
+    kern<<<(unsigned)grid, t.block_threads, smem, st>>>(p);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 template <int AGG, int PATH, bool GSMEM, int UNROLL>
 cudaError_t launch_one(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st) {
     auto kern = k_probe<AGG, PATH, GSMEM, UNROLL>;
@@ -171,6 +263,9 @@ cudaError_t launch_one(const PP &p, const skx_tuning &t, size_t smem, cudaStream
 template <int AGG, int PATH, bool GSMEM>
 cudaError_t launch_unroll(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st, bool vec) {
     if (!vec) return launch_one<AGG, PATH, GSMEM, 0>(p, t, smem, st);
+    // the lean kernel gathers with the default L2 priority (gather_policy 2)
+    if (PATH == kRow8 && p.t_hot == 0 && t.unroll == 1 && p.gather_policy == 2)
+        return launch_r8<AGG, GSMEM>(p, t, smem, st);
     switch (t.unroll) {
         case 1: return launch_one<AGG, PATH, GSMEM, 1>(p, t, smem, st);
         case 4: return launch_one<AGG, PATH, GSMEM, 4>(p, t, smem, st);

@@ -505,6 +505,47 @@ def test_query_copy_layouts(width, offset):
     assert status() == skx.SKX_OK
 
 
+@pytest.mark.parametrize("offset", [0, 1, 3])
+def test_probe_8byte_rows_lean_kernel(offset):
+    """8-byte rows without a hot prefix take a lean kernel (k_probe_r8); it must agree with the
+    oracle for every aggregation and every column arrangement of the pair, with group sums in
+    shared memory (G <= 4096) and in global memory (G > 4096), fk and measure at any offset
+    (head and tail rows), at one to three CTAs per SM, and with the general kernel (two vectors
+    per thread); key and group range errors are still reported."""
+    rng = np.random.default_rng(50 + offset)
+    n, f = 90_001, 700_003
+    rows = np.stack([rng.integers(0, 5000, n), rng.integers(-1000, 100_000, n)], axis=1).astype(np.int32)
+    fk = rng.integers(0, n, f).astype(np.int32)
+    m = rng.integers(-50, 100, f).astype(np.int32)
+    d_rows, d_fk, d_m = dev(rows), offset_view(fk, offset), offset_view(m, offset)
+    cases = [dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=0, filter_lt=4000, group_col=0, num_groups=4000,
+                  payload_col=1),
+             dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=1, filter_lt=50_000, group_col=0, num_groups=5000,
+                  payload_col=-1),
+             dict(agg=oracle.AGG_SUM, filter_col=-1, filter_lt=0, group_col=0, num_groups=1, payload_col=1),
+             dict(agg=oracle.AGG_SUM, filter_col=0, filter_lt=2500, group_col=0, num_groups=1, payload_col=0),
+             dict(agg=oracle.AGG_COUNT, filter_col=1, filter_lt=0, group_col=0, num_groups=1, payload_col=-1)]
+    tunings = [_tuning(hot_keys=-1, lane_keys=-1, ctas_per_sm=c) for c in (1, 2, -1)]
+    tunings.append(_tuning(hot_keys=-1, lane_keys=-1, unroll=2))
+    for d in cases:
+        want = _oracle(rows, fk, m, d)
+        for t in tunings:
+            got = skx.skx_probe_aggregate(d_rows, d_fk, d_m, _q(d), tuning=t)
+            assert np.array_equal(got.cpu().numpy(), want), (d, t.ctas_per_sm, t.unroll)
+    assert status() == skx.SKX_OK
+    bad = fk.copy()
+    bad[[7, f - 1]] = [n, -2]
+    d = cases[0]
+    keep = np.ones(f, bool)
+    keep[[7, f - 1]] = False
+    got = skx.skx_probe_aggregate(d_rows, offset_view(bad, offset), d_m, _q(d), tuning=tunings[2])
+    assert status() == skx.SKX_EKEYRANGE
+    assert np.array_equal(got.cpu().numpy(), _oracle(rows, fk[keep], m[keep], d))
+    d = dict(cases[0], num_groups=3000)  # group keys 3000..3999 pass the filter: out of range
+    skx.skx_probe_aggregate(d_rows, d_fk, d_m, _q(d), tuning=tunings[2])
+    assert status() == skx.SKX_EGROUPRANGE
+
+
 # ------------------------------------------------------------------ Q3a, Q2, maintenance
 @pytest.mark.parametrize("k", [1, 31, 32, 33, 4000, 60_000])
 def test_topk_counts_parity(probe_data, k):
