@@ -58,6 +58,8 @@ def parse_args():
     p.add_argument("--model-l2", default="", help="cache sizes in bytes at which --mode layouts evaluates "
                    "the cache model (default: the device's L2)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--copy", choices=["packed", "query8"], default="packed",
+                   help="the timed step's query copy: 32-bit packed rows (default) or 8-byte rows")
     p.add_argument("--count-method", choices=["auto", "single", "partitioned"], default="auto",
                    help="count algorithm of the timed step (skx_count_ex); the library's automatic choice by default")
     p.add_argument("--tuning", default="",
@@ -87,8 +89,10 @@ def config_of(a, world):
                   "fact inputs (4 GB/step) are also far larger than L2",
             "parallelism": "single GPU" if world == 1 else f"{world} independent replicas",
             "count_method": getattr(a, "count_method", "auto"),
-            "dimension_copy": "the query's permuted 8-byte copy {group or sentinel, payload0} (Section III-B); "
-                              "whole 64-byte rows in alt_step_whole_rows",
+            "dimension_copy": ("the query's permuted copy {group or sentinel, payload0} (Section III-B), packed in "
+                               "32 bits per row beside its 8-byte form (escapes)" if getattr(a, "copy", "packed") ==
+                               "packed" else "the query's permuted 8-byte copy {group or sentinel, payload0} "
+                               "(Section III-B)") + "; whole 64-byte rows in alt_step_whole_rows",
             "probe_tuning": "autotuned" if not getattr(a, "tuning", "") else a.tuning}
 
 
@@ -285,6 +289,8 @@ def run_ours(a, rank, world, local_rank):
     # the Section III-C model's threshold for each layout (skx_split_threshold on the index).
     qp = skx.skx_query_prefiltered(q)
     q8 = torch.empty((a.n, 2), dtype=torch.int32, device=dev)
+    q4 = torch.empty(a.n, dtype=torch.int32, device=dev)
+    packed = a.copy == "packed"
     idx0 = skx.skx_build_index(w.fk, a.n)
     skx.skx_remap(idx0, w.fk, fk2)
     skx.skx_reorder(idx0, w.dim, dim2)
@@ -303,7 +309,8 @@ def run_ours(a, rank, world, local_rank):
     idx0.close()
 
     # The timed step: the query's own permuted copy of the dimension rows (Section III-B: a copy
-    # of the needed columns, permuted by the index; 8 bytes per row, the filter folded in).
+    # of the needed columns, permuted by the index, the filter folded in), packed in 32 bits per
+    # row with the 8-byte copy beside it for rows that do not fit (or 8 bytes per row, --copy).
     def step(ev):
         ev[0].record(stream)
         skx.skx_count_ex(w.fk, a.n, COUNT_METHODS[a.count_method], counts=counts)
@@ -312,9 +319,15 @@ def run_ours(a, rank, world, local_rank):
         ev[2].record(stream)
         skx.skx_remap(idx, w.fk, fk2)
         ev[3].record(stream)
-        skx.skx_reorder_query(idx, w.dim, q, out=q8)
+        if packed:
+            skx.skx_reorder_query_packed(idx, w.dim, q, out8=q8, out4=q4)
+        else:
+            skx.skx_reorder_query(idx, w.dim, q, out=q8)
         ev[4].record(stream)
-        skx.skx_probe_aggregate(q8, fk2, w.measure, qp, out=out, tuning=tuning)
+        if packed:
+            skx.skx_probe_packed(q4, q8, fk2, w.measure, q, out=out)
+        else:
+            skx.skx_probe_aggregate(q8, fk2, w.measure, qp, out=out, tuning=tuning)
         ev[5].record(stream)
         return idx
 
@@ -398,15 +411,23 @@ def run_ours(a, rank, world, local_rank):
     # ---------------- roofline of the dominant kernel
     peak, peak_src = hbm_peak()
     D = expected_distinct(a.n, a.f, a.s)
-    probe_kernel = "k_probe_split+k_probe_deferred" if tuning.split_keys > 0 else "k_probe"
-    # reorder_query reads three 4-byte columns and a perm entry per row and writes 8 bytes;
-    # the probe streams fk and measure (8 bytes a row) and gathers 8 bytes per distinct row
+    if packed:
+        probe_kernel = "k_probe_p4"
+    elif tuning.split_keys > 0:
+        probe_kernel = "k_probe_split+k_probe_deferred"
+    else:
+        probe_kernel = "k_probe_r8" if tuning.hot_keys < 0 and tuning.unroll in (0, 1) else "k_probe"
+    # reorder_query reads three 4-byte columns and a perm entry per row and writes 8 bytes (and
+    # 4 more packed); the probe streams fk and measure (8 bytes a row) and gathers 4 (packed) or
+    # 8 bytes per distinct row
+    row_b = 4 if packed else 8
     alg = {"count": 4 * a.f + 4 * a.n, "sort": 12 * a.n, "remap": 8 * a.f + 4 * a.n,
-           "reorder": 24 * a.n, "probe": 8 * a.f + 8 * D}
+           "reorder": (28 if packed else 24) * a.n, "probe": 8 * a.f + row_b * D}
     kernel_of = {"count": count_kernels(w.fk, a.n, a.f, a.count_method), "sort": "k_radix_*", "remap": "k_remap",
                  "reorder": "k_reorder_query", "probe": probe_kernel}
     traffic_key = {"count": kernel_of["count"], "sort": "k_radix_*", "remap": "k_remap",
-                   "reorder": "k_reorder_query", "probe": "+".join(k + "/query8" for k in probe_kernel.split("+"))}
+                   "reorder": "k_reorder_query" + ("/packed" if packed else ""),
+                   "probe": "+".join(k + ("/query4" if packed else "/query8") for k in probe_kernel.split("+"))}
     stage_avg = {s: statistics.mean(v) for s, v in stage_ms.items()}
     stage_rep = {s: {"ms": round(stage_avg[s], 4), "alg_bytes": int(alg[s]),
                      "gbs": round(alg[s] / (stage_avg[s] * 1e-3) / 1e9, 1),
@@ -418,8 +439,11 @@ def run_ours(a, rank, world, local_rank):
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} hbm_gbs",
                 "alg_bytes_per_launch": int(alg[dom]), "traffic": ncu_traffic(traffic_key[dom], a),
                 "algorithmic_bytes": {"count": "4F + 4N", "sort": "12N (read counts, write perm and rank)",
-                                      "remap": "8F + 4N", "reorder": "24N (3 columns + perm read, 8 B written)",
-                                      "probe": f"8F + 8*D (8-byte query rows), D = expected distinct keys = {D:.4g}"}[dom]}
+                                      "remap": "8F + 4N",
+                                      "reorder": ("28N (3 columns + perm read, 8 + 4 B written)" if packed else
+                                                  "24N (3 columns + perm read, 8 B written)"),
+                                      "probe": f"8F + {row_b}*D ({row_b}-byte query rows), D = expected distinct keys"
+                                               f" = {D:.4g}"}[dom]}
     if roofline["traffic"]:
         # the same launch measured on its actual DRAM bytes (ncu capture, scaled to this workload)
         tgbs = roofline["traffic"] / (stage_avg[dom] * 1e-3) / 1e9
@@ -461,6 +485,8 @@ def run_ours(a, rank, world, local_rank):
                 c16 = skx.skx_reorder_columns(index, w.dim, [0, 1, 2, 3])
                 q8 = skx.skx_reorder_query(index, w.dim, q)
                 narrow[lay] = (c16, q8, keys)
+                p8, p4 = skx.skx_reorder_query_packed(index, w.dim, q)
+                variants[f"{lay}_packed"] = (p4, keys, skx.Tuning(), q, p8)
             for lay, (c16, q8, keys) in narrow.items():
                 remapped = lay == "remapped"
                 t16, _ = skx.skx_probe_autotune(c16, keys, w.measure, q, remapped=remapped,
@@ -473,16 +499,22 @@ def run_ours(a, rank, world, local_rank):
             for name, v in variants.items():
                 rows, keys, tun = v[:3]
                 qq = v[3] if len(v) > 3 else q
+
+                def run_variant(o, rows=rows, keys=keys, tun=tun, qq=qq, v=v):
+                    if len(v) > 4:  # packed rows, escapes in the 8-byte copy v[4]
+                        skx.skx_probe_packed(rows, v[4], keys, w.measure, qq, out=o)
+                    else:
+                        skx.skx_probe_aggregate(rows, keys, w.measure, qq, out=o, tuning=tun)
                 o = torch.empty(1000, dtype=torch.int64, device=dev)
                 for _ in range(2):
                     flush.zero_()
-                    skx.skx_probe_aggregate(rows, keys, w.measure, qq, out=o, tuning=tun)
+                    run_variant(o)
                 ms = []
                 for _ in range(a.sweep_steps):
                     flush.zero_()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    skx.skx_probe_aggregate(rows, keys, w.measure, qq, out=o, tuning=tun)
+                    run_variant(o)
                     e1.record(stream)
                     e1.synchronize()
                     ms.append(e0.elapsed_time(e1))
@@ -492,7 +524,7 @@ def run_ours(a, rank, world, local_rank):
                     for _ in range(a.sweep_steps):
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                         e0.record(stream)
-                        skx.skx_probe_aggregate(rows, keys, w.measure, qq, out=o, tuning=tun)
+                        run_variant(o)
                         e1.record(stream)
                         e1.synchronize()
                         warm.append(e0.elapsed_time(e1))
@@ -506,7 +538,7 @@ def run_ours(a, rank, world, local_rank):
                      "split_model_t": {"rows": tm64, "query8": tm8}}
             for name, ms in times.items():
                 med = statistics.median(ms)
-                gather_b = 8 if name.endswith("query8") else 16
+                gather_b = 4 if name.endswith("packed") else (8 if name.endswith("query8") else 16)
                 gbs = (8 * a.f + gather_b * Ds) / (med * 1e-3) / 1e9
                 tun = variants[name][2]
                 entry[name] = {"ms": round(med, 4), "grows_s": round(a.f / (med * 1e-3) / 1e9, 2),
@@ -546,6 +578,7 @@ def run_ours(a, rank, world, local_rank):
             entry["speedup_remapped_vs_plain"] = round(entry["plain"]["ms"] / entry["remapped"]["ms"], 3)
             entry["speedup_columns16"] = round(entry["plain_columns16"]["ms"] / entry["remapped_columns16"]["ms"], 3)
             entry["speedup_query8"] = round(entry["plain_query8"]["ms"] / entry["remapped_query8"]["ms"], 3)
+            entry["speedup_packed"] = round(entry["plain_packed"]["ms"] / entry["remapped_packed"]["ms"], 3)
             del narrow
             entry["speedup_layout_only"] = round(entry["plain"]["ms"] / entry["remapped_no_hot_prefix"]["ms"], 3)
             entry["model_t_vs_autotuned_ms"] = {"model_t": entry["remapped_split_model_t"]["ms"],
@@ -639,8 +672,8 @@ def run_ours(a, rank, world, local_rank):
         "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded Zipf, generated on device)",
         "config": config_of(a, world), "impl": "ours",
-        "step": "count -> sort by frequency -> remap fk -> the query's permuted 8-byte copy of the dimension rows "
-                "(Section III-B) -> probe (filter + GROUP BY SUM)",
+        "step": "count -> sort by frequency -> remap fk -> the query's permuted copy of the dimension rows "
+                f"(Section III-B; {'32-bit packed' if packed else '8-byte'} rows) -> probe (filter + GROUP BY SUM)",
         "region_s": round(region_s, 3), "gpu_launches": int(launches),
         "roofline": roofline, "stages": stage_rep, "alt_step_whole_rows": alt_step,
         "probe_tuning": {k: tuning.as_dict()[k] for k in ("block_threads", "ctas_per_sm", "unroll", "hot_keys",

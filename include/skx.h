@@ -325,7 +325,11 @@ typedef struct skx_query {
  *   {key, payload}: key = the group (GROUPBY_SUM) or 0 (COUNT, SUM) when the
  *   row passes the filter and the sentinel num_groups (or 1) when it does
  *   not; payload = payload_col (1 for payload_col = -1 or COUNT).  Running
- *   skx_query_prefiltered(q) over that table gives the result of q.
+ *   skx_query_prefiltered(q) over that table gives the result of q.  Every
+ *   row that passes the filter with a group outside [0, num_groups) raises
+ *   SKX_EGROUPRANGE (through skx_stream_status) here, referenced by a fact
+ *   row or not: the prefiltered probe could not tell a group >= num_groups
+ *   from the sentinel.
  * Input and output must not overlap.
  * ------------------------------------------------------------------------ */
 skx_status skx_reorder_columns(const skx_index *idx, const void *d_rows_in, int32_t N, int32_t row_bytes,
@@ -335,6 +339,7 @@ skx_status skx_reorder_query(const skx_index *idx, const void *d_rows_in, int32_
 /* The query to run over a skx_reorder_query table: filter "key < G", group key
  * (column 0), payload (column 1). */
 skx_query skx_query_prefiltered(const skx_query *q);
+
 
 /* Launch and threshold parameters; zero-initialise and set what you need.
  * A field left at 0 takes the library default (chosen from N, F, the query
@@ -368,6 +373,39 @@ typedef struct skx_tuning {
 skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes, const int32_t *d_fk,
                                const int32_t *d_measure, int64_t F, const skx_query *q, int64_t *d_out,
                                const skx_tuning *tuning /* NULL = defaults */, void *stream);
+
+/*
+ * The query copy packed in 32 bits per row (Section III-B's copy of the needed
+ * columns, made as small as the query allows: a row costs 4 bytes of cache
+ * instead of 8, so twice as many rows share a line and the table takes half
+ * the L2).  skx_reorder_query_packed writes the 8-byte copy of
+ * skx_reorder_query to d_out8 (N x 8 bytes) and, in the same pass, d_out4
+ * (N x 4 bytes, 4-byte aligned, overlapping neither d_out8 nor the input):
+ *   d_out4[r] = key << (32 - b) | (payload & (2^(32-b) - 1)),
+ * key = the row's group (GROUP BY; 0 for SUM and COUNT), or G for a row that
+ * fails the filter (G = num_groups for GROUP BY, else 1), payload as a
+ * (32 - b)-bit two's complement number, and b = skx_query_packed_key_bits(q),
+ * the smallest b with 2^b >= G + 2.  A row whose key lies outside [0, G] or
+ * whose payload needs more bits is written with the escape code: the key field
+ * all ones; its values are read from the 8-byte copy when probed.  Errors: as
+ * skx_reorder_query, and SKX_EINVAL for a null or misaligned d_out4 or
+ * overlapping buffers.
+ *
+ * skx_probe_packed joins d_fk / d_measure (keys of the same order as the copy:
+ * d_fk' for a permuted copy) against both tables and gives the result of q
+ * (the original query) in d_out, as skx_probe_aggregate over the 8-byte copy
+ * with skx_query_prefiltered(q) would, exactly.  tuning: only block_threads
+ * and ctas_per_sm are used (NULL: 512 threads, as many CTAs as fit).  Errors:
+ * SKX_EINVAL (bad agg or num_groups, null or misaligned pointer, N < 1,
+ * F >= 2^32); data errors (a key outside [0, N), a group outside [0, G)) as
+ * skx_probe_aggregate, through skx_stream_status.
+ */
+skx_status skx_reorder_query_packed(const skx_index *idx, const void *d_rows_in, int32_t N, int32_t row_bytes,
+                                    const skx_query *q, void *d_out8, uint32_t *d_out4, void *stream);
+int32_t skx_query_packed_key_bits(const skx_query *q); /* b above, or -1 for a bad query */
+skx_status skx_probe_packed(const uint32_t *d_rows4, const void *d_rows8, int32_t N, const int32_t *d_fk,
+                            const int32_t *d_measure, int64_t F, const skx_query *q, int64_t *d_out,
+                            const skx_tuning *tuning, void *stream);
 
 /* The tuning skx_probe_aggregate would use for these arguments when given
  * tuning = NULL (the autotuner's cached choice for this shape if there is

@@ -148,6 +148,11 @@ def lib():
             L.skx_reorder_query.argtypes = [P, P, i32, i32, ctypes.POINTER(Query), P, P]
             L.skx_reorder_query.restype = st
             L.skx_query_prefiltered.argtypes = [ctypes.POINTER(Query)]; L.skx_query_prefiltered.restype = Query
+            L.skx_reorder_query_packed.argtypes = [P, P, i32, i32, ctypes.POINTER(Query), P, P, P]
+            L.skx_reorder_query_packed.restype = st
+            L.skx_query_packed_key_bits.argtypes = [ctypes.POINTER(Query)]; L.skx_query_packed_key_bits.restype = i32
+            L.skx_probe_packed.argtypes = [P, P, i32, P, P, i64, ctypes.POINTER(Query), P, ctypes.POINTER(Tuning), P]
+            L.skx_probe_packed.restype = st
             L.skx_probe_aggregate.argtypes = [P, i32, i32, P, P, i64, ctypes.POINTER(Query), P,
                                               ctypes.POINTER(Tuning), P]
             L.skx_probe_aggregate.restype = st
@@ -425,6 +430,41 @@ def skx_reorder_query(index: Index | None, rows_in, query: Query, out=None, stre
 
 def skx_query_prefiltered(query: Query) -> Query:
     return lib().skx_query_prefiltered(ctypes.byref(query))
+
+
+def skx_reorder_query_packed(index: Index | None, rows_in, query: Query, out8=None, out4=None, stream=None):
+    """The 8-byte query copy and its 32-bit packed form -> (int32[N, 2], int32[N])."""
+    import torch
+    n = rows_in.shape[0]
+    if out8 is None:
+        out8 = torch.empty((n, 2), dtype=torch.int32, device=rows_in.device)
+    if out4 is None:
+        out4 = torch.empty(n, dtype=torch.int32, device=rows_in.device)
+    _check(lib().skx_reorder_query_packed(index._h if index is not None else None, _dptr(rows_in, "rows_in"), n,
+                                          _row_bytes(rows_in), ctypes.byref(query), _dptr(out8, "out8"),
+                                          _dptr(out4, "out4"), _stream(stream)), "skx_reorder_query_packed")
+    return out8, out4
+
+
+def skx_query_packed_key_bits(query: Query) -> int:
+    return lib().skx_query_packed_key_bits(ctypes.byref(query))
+
+
+def skx_probe_packed(rows4, rows8, fk, measure, query: Query, out=None, tuning: Tuning | None = None, stream=None):
+    """The original query's int64 result over the packed copy (escapes read from rows8)."""
+    import torch
+    if out is None:
+        out = torch.empty(query.nout, dtype=torch.int64, device=fk.device)
+    if measure is not None and measure.numel() != fk.numel():
+        raise ValueError("measure must have the same length as fk")
+    if rows8.shape[0] != rows4.shape[0]:
+        raise ValueError("rows4 and rows8 must have the same number of rows")
+    _check(lib().skx_probe_packed(_dptr(rows4, "rows4"), _dptr(rows8, "rows8"), rows4.shape[0],
+                                  _dptr(fk, "fk", torch.int32), _dptr(measure, "measure", torch.int32), fk.numel(),
+                                  ctypes.byref(query), _dptr(out, "out", torch.int64),
+                                  ctypes.byref(tuning) if tuning is not None else None, _stream(stream)),
+           "skx_probe_packed")
+    return out
 
 
 def skx_probe_aggregate(rows, fk, measure, query: Query, out=None, tuning: Tuning | None = None, stream=None):

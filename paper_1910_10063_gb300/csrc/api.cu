@@ -460,8 +460,62 @@ skx_status skx_reorder_query(const skx_index *idx, const void *d_rows_in, int32_
     if (!valid_stream_ptrs(d_rows_in) || (reinterpret_cast<uintptr_t>(d_out) & 7u)) return SKX_EINVAL;
     const char *a = static_cast<const char *>(d_rows_in), *b = static_cast<const char *>(d_out);
     if (a < b + int64_t(N) * 8 && b < a + int64_t(N) * row_bytes) return SKX_EINVAL;
-    SKX_CUDA_TRY(launch_reorder_query(idx ? idx->perm : nullptr, N, d_rows_in, row_bytes, *q, d_out,
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    SKX_CUDA_TRY(launch_reorder_query(idx ? idx->perm : nullptr, N, d_rows_in, row_bytes, *q, d_out, err,
                                       static_cast<cudaStream_t>(stream)));
+    return SKX_OK;
+}
+
+skx_status skx_reorder_query_packed(const skx_index *idx, const void *d_rows_in, int32_t N, int32_t row_bytes,
+                                    const skx_query *q, void *d_out8, uint32_t *d_out4, void *stream) {
+    skx_status s = validate_query(q, row_bytes);
+    if (s != SKX_OK) return s;
+    if (N < 1 || !d_rows_in || !d_out8 || !d_out4 || (idx && idx->N != N)) return SKX_EINVAL;
+    if (!valid_stream_ptrs(d_rows_in) || (reinterpret_cast<uintptr_t>(d_out8) & 7u) ||
+        (reinterpret_cast<uintptr_t>(d_out4) & 3u))
+        return SKX_EINVAL;
+    const char *a = static_cast<const char *>(d_rows_in), *b = static_cast<const char *>(d_out8),
+               *c = reinterpret_cast<const char *>(d_out4);
+    const int64_t la = int64_t(N) * row_bytes, lb = int64_t(N) * 8, lc = int64_t(N) * 4;
+    if ((a < b + lb && b < a + la) || (a < c + lc && c < a + la) || (b < c + lc && c < b + lb)) return SKX_EINVAL;
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    SKX_CUDA_TRY(launch_reorder_query(idx ? idx->perm : nullptr, N, d_rows_in, row_bytes, *q, d_out8, err,
+                                      static_cast<cudaStream_t>(stream), d_out4));
+    return SKX_OK;
+}
+
+int32_t skx_query_packed_key_bits(const skx_query *q) {
+    if (!q || q->agg < SKX_AGG_COUNT || q->agg > SKX_AGG_GROUPBY_SUM) return -1;
+    if (q->agg == SKX_AGG_GROUPBY_SUM && (q->num_groups < 1 || q->num_groups > (1 << 24))) return -1;
+    return packed_key_bits(*q);
+}
+
+skx_status skx_probe_packed(const uint32_t *d_rows4, const void *d_rows8, int32_t N, const int32_t *d_fk,
+                            const int32_t *d_measure, int64_t F, const skx_query *q, int64_t *d_out,
+                            const skx_tuning *tuning, void *stream) {
+    if (skx_query_packed_key_bits(q) < 0) return SKX_EINVAL;
+    if (N < 1 || F < 0 || F >= (int64_t(1) << 32) || !d_out || !d_rows4 || !d_rows8) return SKX_EINVAL;
+    if (F > 0 && (!d_fk || (q->agg != SKX_AGG_COUNT && !d_measure))) return SKX_EINVAL;
+    if (!valid_stream_ptrs(d_fk) || !valid_stream_ptrs(d_measure) || (reinterpret_cast<uintptr_t>(d_rows4) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_rows8) & 7u) || (reinterpret_cast<uintptr_t>(d_out) & 7u))
+        return SKX_EINVAL;
+    unsigned *err = device_error_word();
+    if (!err) return SKX_ENOMEM;
+    ProbeArgs a{};
+    a.rows = d_rows8;
+    a.N = N;
+    a.row_bytes = 8;
+    a.fk = d_fk;
+    a.measure = d_measure;
+    a.F = F;
+    a.q = *q;
+    a.out = d_out;
+    a.err = err;
+    skx_tuning t{};
+    if (tuning) t = *tuning;
+    SKX_CUDA_TRY(launch_probe_packed(a, d_rows4, t, static_cast<cudaStream_t>(stream)));
     return SKX_OK;
 }
 

@@ -221,8 +221,90 @@ __global__ void __launch_bounds__(512, 3) k_probe_r8(PP p) {
 }
 
 template <int AGG, bool GSMEM>
-cudaError_t launch_r8(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st) {
-    auto kern = k_probe_r8<AGG, GSMEM>;
+cudaError_t launch_r8(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st);
+
+// The probe over the packed query copy: 4-byte rows, key = code >> (32 - kbits)
+// (a group, or G for a filtered row), payload = the code's low 32 - kbits bits
+// sign-extended; the escape (key field all ones) reads the row's 8-byte copy
+// (p.rows).  p carries the prefiltered form of the query (filter "key < G" on
+// column 0, group column 0, payload column 1), so each row folds exactly as the
+// probe over the 8-byte copy folds it.  Half the bytes per row: twice as many
+// rows per cache line and a table half the size in L2.
+template <int AGG, bool GSMEM>
+__global__ void __launch_bounds__(512, 3) k_probe_p4(PP p, const uint32_t *__restrict__ rows4, int32_t kbits) {
+    extern __shared__ unsigned long long smem[];
+    GrpRef g;
+    g.lo = reinterpret_cast<uint32_t *>(smem);
+    g.hi = g.lo + (GSMEM ? p.G : 0);
+    if (GSMEM)
+        for (int i = threadIdx.x; i < p.G; i += blockDim.x) smem[i] = 0;
+    __syncthreads();
+    const uint64_t pol_s = policy_evict_first();
+    unsigned long long acc = 0;
+    const int2 *rows8 = reinterpret_cast<const int2 *>(p.rows);
+    const int4 *fk4 = reinterpret_cast<const int4 *>(p.fk + p.head);
+    const int4 *m4 = reinterpret_cast<const int4 *>((AGG == SKX_AGG_COUNT ? p.fk : p.measure) + p.head);
+    const uint32_t nvec = (uint32_t)((p.F - p.head) >> 2);  // F < 2^32
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nthr = gridDim.x * blockDim.x;
+    const uint32_t esc = (1u << kbits) - 1u;
+    // {key, key, payload} of row k from its code c
+    auto decode = [&](uint32_t c, int32_t k) {
+        int4 v;
+        if ((c >> (32 - kbits)) == esc) {
+            const int2 r = __ldg(rows8 + k);
+            v.x = r.x;
+            v.z = r.y;
+        } else {
+            v.x = (int32_t)(c >> (32 - kbits));
+            v.z = (int32_t)(c << kbits) >> kbits;
+        }
+        v.y = v.x;
+        v.w = 0;
+        return v;
+    };
+    int4 nk = make_int4(0, 0, 0, 0), nm = nk;
+    if (tid < nvec) {
+        nk = ld_stream16(fk4 + tid, pol_s);
+        if (AGG != SKX_AGG_COUNT) nm = ld_stream16(m4 + tid, pol_s);
+    }
+    for (uint32_t i = tid; i < nvec; i += nthr) {
+        const int32_t key[4] = {nk.x, nk.y, nk.z, nk.w};
+        const int32_t mea[4] = {nm.x, nm.y, nm.z, nm.w};
+        uint32_t c[4];
+        bool use[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            use[j] = (uint32_t)key[j] < (uint32_t)p.N;
+            c[j] = use[j] ? __ldg(rows4 + key[j]) : 0u;
+        }
+        if (nvec - i > nthr) {
+            nk = ld_stream16(fk4 + (i + nthr), pol_s);
+            if (AGG != SKX_AGG_COUNT) nm = ld_stream16(m4 + (i + nthr), pol_s);
+        }
+        if (!(use[0] && use[1] && use[2] && use[3])) raise_error(p.err, kErrKeyRange);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (use[j]) fold_row<AGG, GSMEM>(p, decode(c[j], key[j]), mea[j], acc, g);
+    }
+    if (tid < 8) {  // unaligned head (< 4 rows) and ragged tail (< 4 rows)
+        const int64_t tail0 = p.head + (int64_t(nvec) << 2);
+        int64_t idx = -1;
+        if (tid < p.head) idx = tid;
+        else if (tid >= 4 && tail0 + (tid - 4) < p.F) idx = tail0 + (tid - 4);
+        if (idx >= 0) {
+            const int32_t k = p.fk[idx];
+            const int32_t m = AGG == SKX_AGG_COUNT ? 0 : p.measure[idx];
+            if ((uint32_t)k < (uint32_t)p.N) fold_row<AGG, GSMEM>(p, decode(__ldg(rows4 + k), k), m, acc, g);
+            else raise_error(p.err, kErrKeyRange);
+        }
+    }
+    flush_groups<AGG, GSMEM>(p, acc, g);
+}
+
+template <typename K, typename... Args>
+cudaError_t launch_lean(K kern, int64_t F, int64_t head, const skx_tuning &t, size_t smem, cudaStream_t st,
+                        Args... args) {
     cudaError_t e = set_smem_limit_once(reinterpret_cast<const void *>(kern), -1);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -230,12 +312,17 @@ cudaError_t launch_r8(const PP &p, const skx_tuning &t, size_t smem, cudaStream_
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (t.ctas_per_sm > 0 && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;
-    const int64_t need = (((p.F - p.head) >> 2) + t.block_threads - 1) / t.block_threads;
+    const int64_t need = (((F - head) >> 2) + t.block_threads - 1) / t.block_threads;
     int64_t grid = int64_t(device_sm_count()) * per_sm;
     if (need < grid) grid = need < 1 ? 1 : need;
-    kern<<<(unsigned)grid, t.block_threads, smem, st>>>(p);
+    kern<<<(unsigned)grid, t.block_threads, smem, st>>>(args...);
     note_launches(1);
     return cudaGetLastError();
+}
+
+template <int AGG, bool GSMEM>
+cudaError_t launch_r8(const PP &p, const skx_tuning &t, size_t smem, cudaStream_t st) {
+    return launch_lean(k_probe_r8<AGG, GSMEM>, p.F, p.head, t, smem, st, p);
 }
 
 template <int AGG, int PATH, bool GSMEM, int UNROLL>
@@ -412,6 +499,64 @@ cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t s
         case SKX_AGG_COUNT: return launch_agg<SKX_AGG_COUNT>(p, path, gsmem, t, smem, st, vec);
         case SKX_AGG_SUM: return launch_agg<SKX_AGG_SUM>(p, path, gsmem, t, smem, st, vec);
         default: return launch_agg<SKX_AGG_GROUPBY_SUM>(p, path, gsmem, t, smem, st, vec);
+    }
+}
+
+cudaError_t launch_probe_packed(const ProbeArgs &a, const uint32_t *rows4, const skx_tuning &t_in, cudaStream_t st) {
+    const skx_query qp = skx_query_prefiltered(&a.q);
+    PP p{};
+    p.fk = a.fk;
+    p.measure = a.measure;
+    p.F = a.F;
+    p.rows = static_cast<const char *>(a.rows);
+    p.N = a.N;
+    p.row_bytes = 8;
+    p.fcol = qp.filter_col;
+    p.flt = qp.filter_lt;
+    p.gcol = qp.group_col;
+    p.G = qp.num_groups;
+    p.pcol = qp.payload_col;
+    p.gather_policy = 2;
+    p.out = reinterpret_cast<unsigned long long *>(a.out);
+    p.err = a.err;
+    const int nout = a.q.agg == SKX_AGG_GROUPBY_SUM ? a.q.num_groups : 1;
+    cudaError_t e = a.accumulate ? cudaSuccess : cudaMemsetAsync(a.out, 0, size_t(nout) * 8, st);
+    if (e != cudaSuccess || a.F <= 0) return e;
+    skx_tuning t = t_in;
+    if (t.block_threads != 128 && t.block_threads != 256 && t.block_threads != 512) t.block_threads = 512;
+    if (t.ctas_per_sm == 0) t.ctas_per_sm = -1;
+    const int32_t kbits = packed_key_bits(a.q);
+    const bool gsmem = a.q.agg == SKX_AGG_GROUPBY_SUM && a.q.num_groups <= kMaxSmemGroups;
+    const size_t smem = gsmem ? size_t(a.q.num_groups) * 8 : 0;
+    const uintptr_t af = reinterpret_cast<uintptr_t>(a.fk) & 15u;
+    const uintptr_t am = a.q.agg == SKX_AGG_COUNT ? af : (reinterpret_cast<uintptr_t>(a.measure) & 15u);
+    if (af == am) {
+        const int64_t mis = (int64_t)(af >> 2);
+        p.head = mis ? (a.F < 4 - mis ? a.F : 4 - mis) : 0;
+    } else {
+        // fk and measure at different offsets mod 16 bytes: the kernel's 16-byte loads cannot
+        // serve both, so the rows are probed through the 8-byte copy instead
+        skx_tuning t8{};
+        t8.block_threads = t.block_threads;
+        t8.ctas_per_sm = t.ctas_per_sm;
+        t8.hot_keys = -1;
+        t8.lane_keys = -1;
+        ProbeArgs a8 = a;
+        a8.row_bytes = 8;
+        a8.q = qp;
+        a8.accumulate = true;
+        resolve_probe_tuning(a8, t8);
+        return launch_probe(a8, t8, st);
+    }
+    switch (a.q.agg) {
+        case SKX_AGG_COUNT:
+            return launch_lean(k_probe_p4<SKX_AGG_COUNT, false>, p.F, p.head, t, smem, st, p, rows4, kbits);
+        case SKX_AGG_SUM:
+            return launch_lean(k_probe_p4<SKX_AGG_SUM, false>, p.F, p.head, t, smem, st, p, rows4, kbits);
+        default:
+            if (gsmem)
+                return launch_lean(k_probe_p4<SKX_AGG_GROUPBY_SUM, true>, p.F, p.head, t, smem, st, p, rows4, kbits);
+            return launch_lean(k_probe_p4<SKX_AGG_GROUPBY_SUM, false>, p.F, p.head, t, smem, st, p, rows4, kbits);
     }
 }
 

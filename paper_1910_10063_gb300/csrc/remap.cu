@@ -238,11 +238,16 @@ __device__ __forceinline__ int32_t pick4(const int4 &c, int i) {
     return i == 0 ? c.x : (i == 1 ? c.y : (i == 2 ? c.z : c.w));
 }
 
+// With out4, each row is also written packed in 32 bits (the query's two values in
+// one word, so that twice as many rows share a cache line): key << (32 - kbits) |
+// the payload's low 32 - kbits bits, key = group or sentinel.  A row whose key is
+// outside [0, sentinel] or whose payload needs more bits gets the escape code
+// (key field all ones); its values stay in the 8-byte copy.
 template <int U, bool VEC>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, VEC ? 4 : 2)
     k_reorder_query(const int32_t *__restrict__ perm, int32_t N, const int32_t *__restrict__ in, int32_t words,
                     int32_t fcol, int32_t flt, int32_t gcol, int32_t pcol, int32_t sentinel, int32_t chunk,
-                    int2 *__restrict__ out) {
+                    int2 *__restrict__ out, uint32_t *__restrict__ out4, int32_t kbits, unsigned *err) {
     const bool wide = words >= 16;  // rows of 64 bytes or more: fetch 64 bytes per miss
     const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
     for (int64_t r0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r0 < N; r0 += nthr * U) {
@@ -278,7 +283,18 @@ __global__ void __launch_bounds__(512)
             const int64_t r = r0 + u * nthr;
             if (r >= N || (uint32_t)src[u] >= (uint32_t)N) continue;
             const bool pass = fcol < 0 || fv[u] < flt;
-            out[r] = make_int2(pass ? gv[u] : sentinel, pv[u]);
+            // a passing row's group must lie in [0, G) (G = sentinel); the probe over the copy
+            // could not tell a group >= G from a filtered row
+            if (pass && gcol >= 0 && (uint32_t)gv[u] >= (uint32_t)sentinel) raise_error(err, kErrGroupRange);
+            const int32_t key = pass ? gv[u] : sentinel;
+            out[r] = make_int2(key, pv[u]);
+            if (out4) {
+                const int pb = 32 - kbits;
+                const int32_t half = int32_t(1) << (pb - 1);
+                const bool fits = (uint32_t)key <= (uint32_t)sentinel && pv[u] >= -half && pv[u] < half;
+                const uint32_t esc = (1u << kbits) - 1u;
+                out4[r] = fits ? ((uint32_t)key << pb) | ((uint32_t)pv[u] & ((1u << pb) - 1u)) : esc << pb;
+            }
         }
     }
 }
@@ -353,8 +369,16 @@ cudaError_t launch_reorder_columns(const int32_t *d_perm, int32_t N, const void 
     return cudaGetLastError();
 }
 
+int32_t packed_key_bits(const skx_query &q) {
+    const int64_t G = q.agg == SKX_AGG_GROUPBY_SUM ? q.num_groups : 1;
+    int32_t b = 1;
+    while ((int64_t(1) << b) < G + 2) ++b;
+    return b;
+}
+
 cudaError_t launch_reorder_query(const int32_t *d_perm, int32_t N, const void *d_in, int32_t row_bytes,
-                                 const skx_query &q, void *d_out, cudaStream_t st) {
+                                 const skx_query &q, void *d_out, unsigned *d_err, cudaStream_t st,
+                                 uint32_t *d_out4) {
     if (N <= 0) return cudaSuccess;
     const bool grp = q.agg == SKX_AGG_GROUPBY_SUM;
     const int32_t sentinel = grp ? q.num_groups : 1;
@@ -371,14 +395,15 @@ cudaError_t launch_reorder_query(const int32_t *d_perm, int32_t N, const void *d
     if (chunk < 0) chunk = 0;
     const int32_t *in = static_cast<const int32_t *>(d_in);
     int2 *out = static_cast<int2 *>(d_out);
-    // 29 registers (VEC) leave room for four 512-thread CTAs per SM, 43 for two
+    // four 512-thread CTAs per SM with one vector load a row (at most 32 registers), two otherwise
     const int grid = grid_for((N + kQueryRows - 1) / kQueryRows, 512, vec ? 4 : 2);
+    const int32_t kbits = packed_key_bits(q);
     if (vec)
         k_reorder_query<kQueryRows, true><<<grid, 512, 0, st>>>(d_perm, N, in, words, fcol, q.filter_lt, gcol, pcol,
-                                                                sentinel, chunk, out);
+                                                                sentinel, chunk, out, d_out4, kbits, d_err);
     else
         k_reorder_query<kQueryRows, false><<<grid, 512, 0, st>>>(d_perm, N, in, words, fcol, q.filter_lt, gcol,
-                                                                 pcol, sentinel, chunk, out);
+                                                                 pcol, sentinel, chunk, out, d_out4, kbits, d_err);
     note_launches(1);
     return cudaGetLastError();
 }

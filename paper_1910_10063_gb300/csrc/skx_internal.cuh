@@ -209,7 +209,11 @@ cudaError_t launch_materialize(const void *d_rows, int32_t N, int32_t row_bytes,
 cudaError_t launch_reorder_columns(const int32_t *d_perm, int32_t N, const void *d_in, int32_t row_bytes,
                                    const int32_t *cols, int32_t ncols, void *d_out, cudaStream_t st);
 cudaError_t launch_reorder_query(const int32_t *d_perm, int32_t N, const void *d_in, int32_t row_bytes,
-                                 const skx_query &q, void *d_out, cudaStream_t st);
+                                 const skx_query &q, void *d_out, unsigned *d_err, cudaStream_t st,
+                                 uint32_t *d_out4 = nullptr);
+// Key bits of the packed query copy: the smallest b with 2^b >= G + 2 (keys 0..G, G the
+// sentinel of a filtered row, and 2^b - 1 the escape), G = num_groups for GROUP BY, else 1.
+int32_t packed_key_bits(const skx_query &q);
 
 struct ProbeArgs {
     const void *rows;
@@ -227,6 +231,9 @@ void resolve_probe_tuning(const ProbeArgs &a, skx_tuning &t);
 // *bshift until there are at most 512 of them, returns their number.
 int32_t split_buckets(int32_t N, int32_t t_split, int32_t *bshift);
 cudaError_t launch_probe(const ProbeArgs &a, const skx_tuning &t, cudaStream_t st);
+// The probe over the packed query copy (a.rows: the 8-byte copy the escapes are read from,
+// a.q: the original query); block_threads and ctas_per_sm of t are used.
+cudaError_t launch_probe_packed(const ProbeArgs &a, const uint32_t *rows4, const skx_tuning &t, cudaStream_t st);
 skx_status validate_query(const skx_query *q, int32_t row_bytes);
 // One unit of a batched probe launch (batch.cu): a query over a contiguous
 // range of remapped fact rows, accumulating into `out`.

@@ -69,6 +69,19 @@ def test_argument_errors_without_gpu():
     assert L.skx_count_ex(P(16), 10, 5, P(16), -1, None) == skx.SKX_EINVAL
     assert L.skx_count_ex(P(16), 1 << 32, 5, P(16), skx.SKX_COUNT_AUTO, None) == skx.SKX_EINVAL
     assert L.skx_count_ex(P(16), 10, (1 << 28) + 1, P(16), skx.SKX_COUNT_PARTITIONED, None) == skx.SKX_ENOTSUP
+    # the packed query copy: key bits b with 2^b >= G + 2, G = num_groups (GROUP BY) or 1
+    for g, bits in ((1, 2), (2, 2), (3, 3), (1000, 10), (1022, 10), (1023, 11), (1 << 24, 25)):
+        assert L.skx_query_packed_key_bits(ctypes.byref(skx.Query(skx.SKX_AGG_GROUPBY_SUM, 1, 50, 0, g, 2))) == bits
+    assert L.skx_query_packed_key_bits(ctypes.byref(skx.Query(skx.SKX_AGG_SUM, 1, 50, 0, 1, 2))) == 2
+    assert L.skx_query_packed_key_bits(ctypes.byref(skx.Query(skx.SKX_AGG_COUNT, 1, 50, 0, 1, -1))) == 2
+    assert L.skx_query_packed_key_bits(ctypes.byref(skx.Query(7, 1, 50, 0, 1, 2))) == -1
+    assert L.skx_query_packed_key_bits(ctypes.byref(skx.Query(skx.SKX_AGG_GROUPBY_SUM, 1, 50, 0, 0, 2))) == -1
+    q = skx.Query.groupby_sum()
+    assert L.skx_reorder_query_packed(None, P(16), 10, 64, ctypes.byref(q), P(16), None, None) == skx.SKX_EINVAL
+    assert L.skx_reorder_query_packed(None, P(16), 10, 64, ctypes.byref(q), P(4096), P(4098), None) == skx.SKX_EINVAL
+    assert L.skx_probe_packed(None, P(16), 10, P(16), P(16), 10, ctypes.byref(q), P(16), None, None) == skx.SKX_EINVAL
+    assert L.skx_probe_packed(P(16), P(16), 10, P(16), P(16), 1 << 32, ctypes.byref(q), P(16), None,
+                              None) == skx.SKX_EINVAL
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

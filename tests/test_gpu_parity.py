@@ -483,7 +483,7 @@ def test_query_copy_layouts(width, offset):
     rows, in both orders (the index's and the identity)."""
     rng = np.random.default_rng(40 + width + offset)
     n = 70_001
-    dim = rng.integers(-50, 150, (n, width)).astype(np.int32)
+    dim = rng.integers(0, 150, (n, width)).astype(np.int32)  # every group in [0, 160)
     fk = rng.integers(0, n, 300_007).astype(np.int32)
     idx = skx.skx_build_index(dev(fk), n)
     _, perm, _ = oracle.build_index(fk, n)
@@ -544,6 +544,88 @@ def test_probe_8byte_rows_lean_kernel(offset):
     d = dict(cases[0], num_groups=3000)  # group keys 3000..3999 pass the filter: out of range
     skx.skx_probe_aggregate(d_rows, d_fk, d_m, _q(d), tuning=tunings[2])
     assert status() == skx.SKX_EGROUPRANGE
+
+
+def _packed_expect(src, d):
+    """The packed copy of rows `src` for query d, written out from the definition in skx.h."""
+    grp = d["agg"] == oracle.AGG_GROUPBY_SUM
+    G = d["num_groups"] if grp else 1
+    b = 1
+    while (1 << b) < G + 2:
+        b += 1
+    pb = 32 - b
+    n = src.shape[0]
+    passes = src[:, d["filter_col"]] < d["filter_lt"] if d["filter_col"] >= 0 else np.ones(n, bool)
+    key = (src[:, d["group_col"]].astype(np.int64) if grp else np.zeros(n, np.int64))
+    key = np.where(passes, key, G)
+    pay = (src[:, d["payload_col"]].astype(np.int64) if (d["payload_col"] >= 0 and d["agg"] != oracle.AGG_COUNT)
+           else np.ones(n, np.int64))
+    fits = (key >= 0) & (key <= G) & (pay >= -(1 << (pb - 1))) & (pay < (1 << (pb - 1)))
+    code = np.where(fits, (key << pb) | (pay & ((1 << pb) - 1)), ((1 << b) - 1) << pb)
+    return code.astype(np.uint32).view(np.int32), key.astype(np.int32), pay.astype(np.int32)
+
+
+@pytest.mark.parametrize("offset_m", [0, 1])
+def test_packed_query_copy_and_probe(offset_m):
+    """The 32-bit packed query copy, element by element against its definition over the oracle's
+    permuted rows (payloads that fit and that escape, negative ones, groups outside [0, G) that
+    escape, G on both sides of a power of two, shared and global group sums), and the probe over
+    it exactly equal to the oracle's join on the original layout; measure at the key column's
+    offset (16-byte path) and at another (the 8-byte copy's path); range errors reported."""
+    rng = np.random.default_rng(60 + offset_m)
+    n, f = 50_003, 600_007
+    dim = np.stack([rng.integers(0, 1100, n), rng.integers(0, 100, n), rng.integers(-3000, 3000, n),
+                    rng.integers(0, 10, n)], axis=1).astype(np.int32)
+    big = rng.random(n) < 0.02
+    dim[big, 2] = rng.integers(-2_000_000_000, 2_000_000_000, int(big.sum()))  # payloads that escape
+    fk = rng.integers(0, n, f).astype(np.int32)
+    m = rng.integers(-100, 100, f).astype(np.int32)
+    idx = skx.skx_build_index(dev(fk), n)
+    _, perm, rank = oracle.build_index(fk, n)
+    src = oracle.reorder(perm, dim)
+    fk2 = oracle.remap(rank, fk)
+    d_fk2 = offset_view(fk2, 1)
+    d_m = offset_view(m, 1 + offset_m)
+    d_dim = dev(dim)
+    cases = [dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=1, filter_lt=50, group_col=0, num_groups=1100, payload_col=2),
+             dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=1, filter_lt=90, group_col=3, num_groups=1022, payload_col=2),
+             dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=-1, filter_lt=0, group_col=3, num_groups=1023, payload_col=0),
+             dict(agg=oracle.AGG_GROUPBY_SUM, filter_col=1, filter_lt=70, group_col=0, num_groups=5000, payload_col=2),
+             dict(agg=oracle.AGG_SUM, filter_col=1, filter_lt=30, group_col=0, num_groups=1, payload_col=2),
+             dict(agg=oracle.AGG_COUNT, filter_col=1, filter_lt=30, group_col=0, num_groups=1, payload_col=-1)]
+    for d in cases:
+        q = _q(d)
+        rows8, rows4 = skx.skx_reorder_query_packed(idx, d_dim, q)
+        code, key, pay = _packed_expect(src, d)
+        assert np.array_equal(rows4.cpu().numpy(), code), d
+        assert np.array_equal(rows8.cpu().numpy()[:, 0], key) and np.array_equal(rows8.cpu().numpy()[:, 1], pay)
+        want = _oracle(dim, fk, m, d)
+        for t in (None, _tuning(ctas_per_sm=1), _tuning(block_threads=256)):
+            got = skx.skx_probe_packed(rows4, rows8, d_fk2, d_m, q, tuning=t)
+            assert np.array_equal(got.cpu().numpy(), want), (d, t)
+        assert status() == skx.SKX_OK
+    # group keys 1000..1099 pass the filter: outside [0, 1000); the copy reports it
+    d = dict(cases[0], num_groups=1000)
+    rows8, rows4 = skx.skx_reorder_query_packed(idx, d_dim, _q(d))
+    assert status() == skx.SKX_EGROUPRANGE
+    rows8 = skx.skx_reorder_query(idx, d_dim, _q(d))
+    assert status() == skx.SKX_EGROUPRANGE
+    # a negative group escapes the packing and the probe reports it too
+    neg = dim.copy()
+    neg[dim[:, 1] < 50, 0] = -5
+    rows8, rows4 = skx.skx_reorder_query_packed(idx, dev(neg), _q(cases[0]))
+    assert status() == skx.SKX_EGROUPRANGE
+    skx.skx_probe_packed(rows4, rows8, d_fk2, d_m, _q(cases[0]))
+    assert status() == skx.SKX_EGROUPRANGE
+    bad = fk2.copy()
+    bad[[3, f - 2]] = [n, -1]
+    d = cases[0]
+    rows8, rows4 = skx.skx_reorder_query_packed(idx, d_dim, _q(d))
+    got = skx.skx_probe_packed(rows4, rows8, offset_view(bad, 1), d_m, _q(d))
+    assert status() == skx.SKX_EKEYRANGE
+    keep = np.ones(f, bool)
+    keep[[3, f - 2]] = False
+    assert np.array_equal(got.cpu().numpy(), _oracle(dim, fk[keep], m[keep], d))
 
 
 # ------------------------------------------------------------------ Q3a, Q2, maintenance
