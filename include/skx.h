@@ -639,11 +639,11 @@ void skx_server_destroy(skx_server *s);
  * Whole path from host memory (Sections III-A, III-B and IV in sequence):
  * copies h_fk[F], h_measure[F] and the dimension table h_rows[N * row_bytes]
  * to the device, builds the index, remaps the keys, builds the query's
- * permuted copy of the dimension rows (skx_reorder_query: 8 bytes per row,
- * Section III-B), runs the query on it and copies the result (num_groups
- * or 1 int64) to h_out.  The probe uses the autotuner's cached choice for
- * (N, 8-byte rows, the prefiltered query) when there is one.  Device buffers are stream-ordered allocations on
- * `stream`, released before return.  Synchronous: returns after h_out is
+ * permuted copy of the dimension rows (skx_reorder_query_packed: 32 bits
+ * per row beside its 8-byte form, Section III-B), runs the query on it
+ * (skx_probe_packed) and copies the result (num_groups or 1 int64) to h_out.
+ * Device buffers (N * (row_bytes + 12) + 8 F bytes and the index) are
+ * stream-ordered allocations on `stream`, released before return.  Synchronous: returns after h_out is
  * written, with any data error of this call already reported (SKX_EKEYRANGE,
  * SKX_EGROUPRANGE) rather than left for skx_stream_status.
  * ------------------------------------------------------------------------ */

@@ -624,14 +624,17 @@ skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_by
     const bool with_m = F > 0 && q->agg != SKX_AGG_COUNT;
     const int nm = with_m ? kChunks : 0;
     char *d_rows = nullptr, *d_rows2 = nullptr;
+    uint32_t *d_rows4 = nullptr;
     int32_t *d_fk = nullptr, *d_m = nullptr;
     int64_t *d_out = nullptr;
     skx_index *idx = nullptr;
     cudaEvent_t ev_alloc = nullptr, ev_fk = nullptr, ev_rows = nullptr, ev_done = nullptr, ev_m[kChunks] = {};
-    // the probe runs over the query's own permuted copy (Section III-B): 8 bytes per
-    // dimension row, {group or the filter's sentinel, payload}
+    // the probe runs over the query's own permuted copy (Section III-B): {group or the
+    // filter's sentinel, payload} packed in 32 bits per dimension row, with its 8-byte form
+    // beside it for the rows that do not fit
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows), rows_b, st);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows2), size_t(N) * 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_rows4), size_t(N) * 4, st);
     if (e == cudaSuccess && F > 0) e = cudaMallocAsync(reinterpret_cast<void **>(&d_fk), fk_b, st);
     if (e == cudaSuccess && with_m) e = cudaMallocAsync(reinterpret_cast<void **>(&d_m), fk_b, st);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_out), size_t(nout) * 8, st);
@@ -663,17 +666,16 @@ skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_by
     if (s == SKX_OK) s = skx_build_index(d_fk, F, N, stream, &idx);
     if (s == SKX_OK) s = skx_remap(idx, d_fk, d_fk, F, stream);
     if (s == SKX_OK) s = cudaStreamWaitEvent(st, ev_rows, 0) == cudaSuccess ? SKX_OK : SKX_ECUDA;
-    if (s == SKX_OK) s = skx_reorder_query(idx, d_rows, N, row_bytes, q, d_rows2, stream);
+    if (s == SKX_OK) s = skx_reorder_query_packed(idx, d_rows, N, row_bytes, q, d_rows2, d_rows4, stream);
     if (s == SKX_OK) {
         ProbeArgs a{};
         a.rows = d_rows2;
         a.N = N;
         a.row_bytes = 8;
-        a.q = skx_query_prefiltered(q);
+        a.q = *q;
         a.out = d_out;
         a.err = err;
-        skx_tuning t{};
-        cached_probe_tuning(N, 8, a.q, F, 1, &t);
+        skx_tuning t{};  // 512 threads, as many CTAs as fit
         const int parts = with_m ? nm : 1;
         for (int k = 0; k < parts && s == SKX_OK; ++k) {
             const int64_t a0 = with_m ? cut(k) : 0, a1 = with_m ? cut(k + 1) : F;
@@ -682,10 +684,8 @@ skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_by
             a.measure = d_m ? d_m + a0 : nullptr;
             a.F = a1 - a0;
             a.accumulate = k > 0;
-            skx_tuning tk = t;
-            resolve_probe_tuning(a, tk);
             if (s == SKX_OK) {
-                e = launch_probe(a, tk, st);
+                e = launch_probe_packed(a, d_rows4, t, st);
                 if (e != cudaSuccess) s = cuda_status(e);
             }
         }
@@ -699,6 +699,7 @@ skx_status skx_join_aggregate_host(const void *h_rows, int32_t N, int32_t row_by
     skx_index_destroy(idx);
     if (d_rows) cudaFreeAsync(d_rows, st);
     if (d_rows2) cudaFreeAsync(d_rows2, st);
+    if (d_rows4) cudaFreeAsync(d_rows4, st);
     if (d_fk) cudaFreeAsync(d_fk, st);
     if (d_m) cudaFreeAsync(d_m, st);
     if (d_out) cudaFreeAsync(d_out, st);

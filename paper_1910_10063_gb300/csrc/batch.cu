@@ -49,7 +49,7 @@ __global__ void k_batch_clear(const BatchDesc *__restrict__ desc, int32_t n, uin
 }
 
 template <int AGG, int PATH>
-__device__ __forceinline__ void batch_rows(const PP &p, unsigned long long &acc, unsigned long long *s_grp,
+__device__ __forceinline__ void batch_rows(const PP &p, unsigned long long &acc, GrpRef g,
                                            const HotArrays &h, uint64_t pol_s, uint64_t pol_g, bool vec) {
     const unsigned lane = lane_id();
     if (vec) {
@@ -78,7 +78,7 @@ __device__ __forceinline__ void batch_rows(const PP &p, unsigned long long &acc,
                 if (AGG != SKX_AGG_COUNT) nm = ld_stream16(m4 + nv, pol_s);
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) handle<AGG, PATH, true>(p, key[j], mea[j], row[j], acc, s_grp, h, lane);
+            for (int j = 0; j < 4; ++j) handle_row<AGG, PATH, true>(p, key[j], mea[j], row[j], acc, g, h, lane);
         }
         const int64_t tail0 = nvec << 2;
         if (threadIdx.x < p.F - tail0) {
@@ -87,7 +87,7 @@ __device__ __forceinline__ void batch_rows(const PP &p, unsigned long long &acc,
             const int32_t m = AGG == SKX_AGG_COUNT ? 0 : p.measure[i];
             int4 row = make_int4(0, 0, 0, 0);
             if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N) row = fetch_row<PATH, AGG>(p, k, pol_g);
-            handle<AGG, PATH, true>(p, k, m, row, acc, s_grp, h, lane);
+            handle_row<AGG, PATH, true>(p, k, m, row, acc, g, h, lane);
         }
     } else {
         for (int64_t i = threadIdx.x; i < p.F; i += blockDim.x) {
@@ -95,13 +95,13 @@ __device__ __forceinline__ void batch_rows(const PP &p, unsigned long long &acc,
             const int32_t m = AGG == SKX_AGG_COUNT ? 0 : ld_stream4(p.measure + i, pol_s);
             int4 row = make_int4(0, 0, 0, 0);
             if ((uint32_t)k >= (uint32_t)p.t_hot && (uint32_t)k < (uint32_t)p.N) row = fetch_row<PATH, AGG>(p, k, pol_g);
-            handle<AGG, PATH, true>(p, k, m, row, acc, s_grp, h, lane);
+            handle_row<AGG, PATH, true>(p, k, m, row, acc, g, h, lane);
         }
     }
 }
 
 template <int AGG, int PATH>
-__device__ __forceinline__ void batch_epilogue(const PP &p, unsigned long long acc, unsigned long long *s_grp,
+__device__ __forceinline__ void batch_epilogue(const PP &p, unsigned long long acc, GrpRef g,
                                                const HotArrays &h, uint64_t pol_g, unsigned long long *s_red) {
     for (int k = threadIdx.x; k < p.t_hot; k += blockDim.x) {
         unsigned long long s = hot_value(h.lo[k], h.hi[k]);
@@ -110,12 +110,14 @@ __device__ __forceinline__ void batch_epilogue(const PP &p, unsigned long long a
             for (int l = 0; l < 32; ++l) s += hot_value(h.lane_lo[(size_t(k) << 5) + l], h.lane_hi[(size_t(k) << 5) + l]);
         }
         if (s == 0) continue;
-        fold<AGG, true>(p, fetch_row<PATH, AGG>(p, k, pol_g), s, acc, s_grp);
+        fold_sum<AGG, true>(p, fetch_row<PATH, AGG>(p, k, pol_g), s, acc, g);
     }
     if (AGG == SKX_AGG_GROUPBY_SUM) {
         __syncthreads();
-        for (int g = threadIdx.x; g < p.G; g += blockDim.x)
-            if (s_grp[g]) atomicAdd(p.out + g, s_grp[g]);
+        for (int k = threadIdx.x; k < p.G; k += blockDim.x) {
+            const unsigned long long v = (unsigned long long)g.lo[k] + ((unsigned long long)g.hi[k] << 32);
+            if (v) atomicAdd(p.out + k, v);
+        }
     } else {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -136,7 +138,10 @@ __global__ void __launch_bounds__(512) k_probe_batch(BatchArgs a) {
     __shared__ int32_t s_q;
     __shared__ BatchDesc s_d;
     __shared__ unsigned long long s_red[16];
-    unsigned long long *s_grp = smem;
+    // group sums: two 32-bit words per group slot (low word, and high word with the carries)
+    GrpRef g;
+    g.lo = reinterpret_cast<uint32_t *>(smem);
+    g.hi = g.lo + a.max_groups;
     HotArrays h;
     h.lo = reinterpret_cast<uint32_t *>(smem + a.max_groups);
     h.hi = reinterpret_cast<int32_t *>(h.lo + a.t_hot);
@@ -191,19 +196,19 @@ __global__ void __launch_bounds__(512) k_probe_batch(BatchArgs a) {
         const bool vec = d.vec != 0;
         switch (d.agg) {
             case SKX_AGG_COUNT:
-                batch_rows<SKX_AGG_COUNT, PATH>(p, acc, s_grp, h, pol_s, pol_g, vec);
+                batch_rows<SKX_AGG_COUNT, PATH>(p, acc, g, h, pol_s, pol_g, vec);
                 __syncthreads();
-                batch_epilogue<SKX_AGG_COUNT, PATH>(p, acc, s_grp, h, pol_g, s_red);
+                batch_epilogue<SKX_AGG_COUNT, PATH>(p, acc, g, h, pol_g, s_red);
                 break;
             case SKX_AGG_SUM:
-                batch_rows<SKX_AGG_SUM, PATH>(p, acc, s_grp, h, pol_s, pol_g, vec);
+                batch_rows<SKX_AGG_SUM, PATH>(p, acc, g, h, pol_s, pol_g, vec);
                 __syncthreads();
-                batch_epilogue<SKX_AGG_SUM, PATH>(p, acc, s_grp, h, pol_g, s_red);
+                batch_epilogue<SKX_AGG_SUM, PATH>(p, acc, g, h, pol_g, s_red);
                 break;
             default:
-                batch_rows<SKX_AGG_GROUPBY_SUM, PATH>(p, acc, s_grp, h, pol_s, pol_g, vec);
+                batch_rows<SKX_AGG_GROUPBY_SUM, PATH>(p, acc, g, h, pol_s, pol_g, vec);
                 __syncthreads();
-                batch_epilogue<SKX_AGG_GROUPBY_SUM, PATH>(p, acc, s_grp, h, pol_g, s_red);
+                batch_epilogue<SKX_AGG_GROUPBY_SUM, PATH>(p, acc, g, h, pol_g, s_red);
                 break;
         }
         __syncthreads();

@@ -69,31 +69,6 @@ __device__ __forceinline__ int4 fetch_row(const PP &p, int32_t k, uint64_t pol) 
 
 __device__ __forceinline__ bool passes(const PP &p, const int4 &v) { return p.fcol < 0 || v.x < p.flt; }
 
-// Fold `amount` (a measure, a hot-key measure sum, or a count) for a row whose
-// gathered values are v.
-template <int AGG, bool GSMEM>
-__device__ __forceinline__ void fold(const PP &p, const int4 &v, unsigned long long amount, unsigned long long &acc,
-                                     unsigned long long *s_grp) {
-    if (!passes(p, v)) return;
-    if (AGG == SKX_AGG_COUNT) {
-        acc += amount;
-        return;
-    }
-    const unsigned long long prod = amount * (unsigned long long)(long long)v.z;
-    if (AGG == SKX_AGG_SUM) {
-        acc += prod;
-        return;
-    }
-    if ((uint32_t)v.y < (uint32_t)p.G) {
-        if (GSMEM)
-            atomicAdd(s_grp + v.y, prod);
-        else
-            atomicAdd(p.out + v.y, prod);
-    } else {
-        raise_error(p.err, kErrGroupRange);
-    }
-}
-
 // Hot-key sums are kept exactly in two 32-bit shared words (32-bit shared
 // atomics run about 4x faster than 64-bit ones on this part): lo accumulates
 // the measures as unsigned 32-bit values, hi counts the wrap-arounds of lo
@@ -284,7 +259,9 @@ __device__ __forceinline__ void hot_add4(const PP &p, const HotArrays &h, const 
     }
 }
 
-// handle() with the 32-bit group sums (the single and split probes).
+// One fact row: a hot key's measure goes to its shared per-key sum, any other
+// key's row (already gathered) is folded into the group sums (the single,
+// split and batched probes).
 template <int AGG, int PATH, bool GSMEM>
 __device__ __forceinline__ void handle_row(const PP &p, int32_t k, int32_t m, const int4 &row, unsigned long long &acc,
                                            GrpRef g, const HotArrays &h, unsigned lane) {
@@ -297,24 +274,6 @@ __device__ __forceinline__ void handle_row(const PP &p, int32_t k, int32_t m, co
         }
     } else if ((uint32_t)k < (uint32_t)p.N) {
         fold_row<AGG, GSMEM>(p, row, m, acc, g);
-    } else {
-        raise_error(p.err, kErrKeyRange);
-    }
-}
-
-template <int AGG, int PATH, bool GSMEM>
-__device__ __forceinline__ void handle(const PP &p, int32_t k, int32_t m, const int4 &row, unsigned long long &acc,
-                                       unsigned long long *s_grp, const HotArrays &h, unsigned lane) {
-    if ((uint32_t)k < (uint32_t)p.t_hot) {
-        if ((uint32_t)k < (uint32_t)p.t_lane) {
-            const size_t i = (size_t(k) << 5) + lane;
-            hot_add<AGG>(HotRef{h.lane_lo + i, h.lane_hi + i}, m);
-        } else {
-            hot_add<AGG>(HotRef{h.lo + k, h.hi + k}, m);
-        }
-    } else if ((uint32_t)k < (uint32_t)p.N) {
-        const unsigned long long amount = AGG == SKX_AGG_COUNT ? 1ull : (unsigned long long)(long long)m;
-        fold<AGG, GSMEM>(p, row, amount, acc, s_grp);
     } else {
         raise_error(p.err, kErrKeyRange);
     }

@@ -38,10 +38,10 @@ def _shape_args(rec):
 def test_ncu_traffic_lookup(tmp_path, monkeypatch):
     with open(bench.TRAFFIC_PATH) as fh:
         table = json.load(fh)
-    rec = table["k_probe/query8"]
+    rec = table["k_probe_p4/query4"]
     a = _shape_args(rec)
     # the committed entry is used only while its kernel sources are unchanged
-    live = bench.ncu_traffic("k_probe/query8", a)
+    live = bench.ncu_traffic("k_probe_p4/query4", a)
     same = bench.source_sha([bench.os.path.join(bench.ROOT, x) for x in rec["sources"]]) == rec["source_sha"]
     assert live == (rec["bytes_per_launch"] if same else None)
 
