@@ -599,8 +599,10 @@ __global__ void __launch_bounds__(kPBlock)
         return;
     }
     uint32_t c_own = 0;  // sampled keys of bucket threadIdx.x
-    if ((int)threadIdx.x < B)
+    if ((int)threadIdx.x < B) {
+#pragma unroll 16
         for (int c = 0; c < kPlanCtas; ++c) c_own += smat[size_t(c) * (B + 1) + threadIdx.x];
+    }
     if (threadIdx.x < 32) {  // sampled keys outside [0, N): column B
         uint32_t v = 0;
         for (int c = lane_id(); c < kPlanCtas; c += 32) v += smat[size_t(c) * (B + 1) + B];

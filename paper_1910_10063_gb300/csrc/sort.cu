@@ -86,27 +86,28 @@ __global__ void __launch_bounds__(kSortBlock)
     // a length read from the device that exceeds the grid (more heavy ids than the
     // bound F / 255 allows) would leave ids unsorted: report it
     if (n_dev && blockIdx.x == 0 && threadIdx.x == 0 && n > gridDim.x * kTile) raise_error(err, kErrCountBound);
-    for (int i = threadIdx.x; i < kBins; i += kSortBlock) s_hist[i] = 0;
-    __syncthreads();
     const uint32_t tile = blockIdx.x;
     const uint32_t base = tile * kTile + warp * (32 * kRounds);
-    if (tile * kTile < n) {  // tiles past the end (heavy passes) publish zero counts
-        // all of the warp's loads first, so their latencies overlap; then the ranking rounds
-        uint32_t dig[kRounds];
-        bool over = false;
+    const bool live = tile * kTile < n;  // tiles past the end (heavy passes) publish zero counts
+    // the keys are loaded first, so that their latency overlaps the histogram's clearing
+    uint32_t dig[kRounds];
+    bool over = false;
 #pragma unroll
-        for (int r = 0; r < kRounds; ++r) {
-            const uint32_t i = base + r * 32 + lane;
-            dig[r] = kBins;  // sentinel for lanes past the end
-            if (i < n) {
-                uint32_t key, val;
-                load_key<SRC>(cnt, keys_in, vals_in, i, key, val);
-                dig[r] = (key >> shift) & (kBins - 1);
-                // the first pass reads every count: one above the bound F would be
-                // truncated to the sorted key bits
-                if ((SRC == kSrcClamped || SRC == kSrcCounts) && cnt[i] > cmax) over = true;
-            }
+    for (int r = 0; r < kRounds; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        dig[r] = kBins;  // sentinel for lanes past the end
+        if (live && i < n) {
+            uint32_t key, val;
+            load_key<SRC>(cnt, keys_in, vals_in, i, key, val);
+            dig[r] = (key >> shift) & (kBins - 1);
+            // the first pass reads every count: one above the bound F would be
+            // truncated to the sorted key bits
+            if ((SRC == kSrcClamped || SRC == kSrcCounts) && cnt[i] > cmax) over = true;
         }
+    }
+    for (int i = threadIdx.x; i < kBins; i += kSortBlock) s_hist[i] = 0;
+    __syncthreads();
+    if (live) {
         if (over) raise_error(err, kErrCountBound);
 #pragma unroll
         for (int r = 0; r < kRounds; ++r) {
@@ -225,13 +226,10 @@ __global__ void __launch_bounds__(kSortBlock)
     const uint32_t tile = blockIdx.x;
     if (tile * kTile >= n) return;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
-    for (int i = threadIdx.x; i < kWarps * kBins; i += kSortBlock) (&s_cnt[0][0])[i] = 0;
-    for (int d = threadIdx.x; d < kBins; d += kSortBlock) s_base[d] = tile_off[(size_t)d * num_tiles + tile];
-    __syncthreads();
-
     const uint32_t base = tile * kTile + warp * (32 * kRounds);
     uint32_t key[kRounds], val[kRounds], loc[kRounds];
-    // all of the warp's loads first, so their latencies overlap; then the ranking rounds
+    // all of the warp's loads first, so their latencies overlap (with each other and with the
+    // tile offsets' loads below); then the ranking rounds
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const uint32_t i = base + r * 32 + lane;
@@ -239,6 +237,9 @@ __global__ void __launch_bounds__(kSortBlock)
         val[r] = 0;
         if (i < n) load_key<SRC>(cnt, keys_in, vals_in, i, key[r], val[r]);
     }
+    for (int i = threadIdx.x; i < kWarps * kBins; i += kSortBlock) (&s_cnt[0][0])[i] = 0;
+    for (int d = threadIdx.x; d < kBins; d += kSortBlock) s_base[d] = tile_off[(size_t)d * num_tiles + tile];
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const uint32_t i = base + r * 32 + lane;
