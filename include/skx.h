@@ -384,7 +384,8 @@ skx_status skx_probe_aggregate(const void *d_rows, int32_t N, int32_t row_bytes,
  *   d_out4[r] = key << (32 - b) | (payload & (2^(32-b) - 1)),
  * key = the row's group (GROUP BY; 0 for SUM and COUNT), or G for a row that
  * fails the filter (G = num_groups for GROUP BY, else 1), payload as a
- * (32 - b)-bit two's complement number, and b = skx_query_packed_key_bits(q),
+ * (32 - b)-bit two's complement number (0 for a row that fails the filter:
+ * it is never used), and b = skx_query_packed_key_bits(q),
  * the smallest b with 2^b >= G + 2.  A row whose key lies outside [0, G] or
  * whose payload needs more bits is written with the escape code: the key field
  * all ones; its values are read from the 8-byte copy when probed.  Errors: as

@@ -240,7 +240,7 @@ __device__ __forceinline__ int32_t pick4(const int4 &c, int i) {
 
 // With out4, each row is also written packed in 32 bits (the query's two values in
 // one word, so that twice as many rows share a cache line): key << (32 - kbits) |
-// the payload's low 32 - kbits bits, key = group or sentinel.  A row whose key is
+// the payload's low 32 - kbits bits (0 for a filtered row), key = group or sentinel.  A row whose key is
 // outside [0, sentinel] or whose payload needs more bits gets the escape code
 // (key field all ones); its values stay in the 8-byte copy.
 template <int U, bool VEC>
@@ -288,12 +288,13 @@ __global__ void __launch_bounds__(512, VEC ? 4 : 2)
             if (pass && gcol >= 0 && (uint32_t)gv[u] >= (uint32_t)sentinel) raise_error(err, kErrGroupRange);
             const int32_t key = pass ? gv[u] : sentinel;
             out[r] = make_int2(key, pv[u]);
-            if (out4) {
+            if (out4) {  // a filtered row's payload is never used: it is packed as 0
                 const int pb = 32 - kbits;
                 const int32_t half = int32_t(1) << (pb - 1);
-                const bool fits = (uint32_t)key <= (uint32_t)sentinel && pv[u] >= -half && pv[u] < half;
+                const int32_t pay = pass ? pv[u] : 0;
+                const bool fits = (uint32_t)key <= (uint32_t)sentinel && pay >= -half && pay < half;
                 const uint32_t esc = (1u << kbits) - 1u;
-                out4[r] = fits ? ((uint32_t)key << pb) | ((uint32_t)pv[u] & ((1u << pb) - 1u)) : esc << pb;
+                out4[r] = fits ? ((uint32_t)key << pb) | ((uint32_t)pay & ((1u << pb) - 1u)) : esc << pb;
             }
         }
     }

@@ -560,8 +560,9 @@ def _packed_expect(src, d):
     key = np.where(passes, key, G)
     pay = (src[:, d["payload_col"]].astype(np.int64) if (d["payload_col"] >= 0 and d["agg"] != oracle.AGG_COUNT)
            else np.ones(n, np.int64))
-    fits = (key >= 0) & (key <= G) & (pay >= -(1 << (pb - 1))) & (pay < (1 << (pb - 1)))
-    code = np.where(fits, (key << pb) | (pay & ((1 << pb) - 1)), ((1 << b) - 1) << pb)
+    pay_code = np.where(passes, pay, 0)  # a filtered row's payload is packed as 0
+    fits = (key >= 0) & (key <= G) & (pay_code >= -(1 << (pb - 1))) & (pay_code < (1 << (pb - 1)))
+    code = np.where(fits, (key << pb) | (pay_code & ((1 << pb) - 1)), ((1 << b) - 1) << pb)
     return code.astype(np.uint32).view(np.int32), key.astype(np.int32), pay.astype(np.int32)
 
 
