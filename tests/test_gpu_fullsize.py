@@ -102,10 +102,16 @@ def test_large_probe_exact(large, s):
     got = skx.skx_probe_aggregate(dim2, fk2, w.measure, q, tuning=t).cpu().numpy()
     want = oracle.probe(w.dim.cpu().numpy(), fk.cpu().numpy(), w.measure.cpu().numpy(), nthreads=THREADS)
     assert np.array_equal(got, want)
-    # the query copy path gives the same result
+    # the query copy path gives the same result: 8-byte rows (the lean kernel's launch, no hot
+    # prefix), and the packed copy with the bench's launch (512 threads, as many CTAs as fit)
     q8 = skx.skx_reorder_query(idx, w.dim, q)
-    got8 = skx.skx_probe_aggregate(q8, fk2, w.measure, skx.skx_query_prefiltered(q)).cpu().numpy()
+    got8 = skx.skx_probe_aggregate(q8, fk2, w.measure, skx.skx_query_prefiltered(q),
+                                   tuning=skx.Tuning.plain()).cpu().numpy()
     assert np.array_equal(got8, want)
+    p8, p4 = skx.skx_reorder_query_packed(idx, w.dim, q)
+    assert torch.equal(p8, q8)
+    gotp = skx.skx_probe_packed(p4, p8, fk2, w.measure, q).cpu().numpy()
+    assert np.array_equal(gotp, want)
     idx.close()
     assert skx.skx_stream_status() == skx.SKX_OK
 
