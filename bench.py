@@ -408,6 +408,48 @@ def run_ours(a, rank, world, local_rank):
                                                                              "hot_keys", "lane_keys", "split_keys")},
                     "split_model_t": t_model["rows64"]}
 
+    # ---------------- end to end through the host-buffer C-ABI call (measured right after the
+    # timed step, before the sweep, batch and serving sections)
+    e2e = None
+    if not a.no_e2e:
+        h_dim = torch.empty(w.dim.shape, dtype=torch.int32, pin_memory=True)
+        h_fk = torch.empty(a.f, dtype=torch.int32, pin_memory=True)
+        h_m = torch.empty(a.f, dtype=torch.int32, pin_memory=True)
+        h_dim.copy_(w.dim)
+        h_fk.copy_(w.fk)
+        h_m.copy_(w.measure)
+        h_out = np.zeros(1000, dtype=np.int64)
+        skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
+        if not np.array_equal(h_out, result):
+            raise RuntimeError("host-buffer path disagrees with the device-resident path")
+        for _ in range(max(0, a.warmup - 1)):  # the checked call above is the first warm-up
+            skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
+        n_e2e = max(3, min(a.steps, 10))
+        # as timeit does: no cyclic garbage collection of the bench's own objects inside the
+        # timed calls (a full collection over this process's heap takes up to ~100 ms)
+        gc.collect()
+        gc_was = gc.isenabled()
+        gc.disable()
+        barrier()
+        t = []
+        try:
+            for _ in range(n_e2e):
+                t0 = time.perf_counter()
+                skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
+                t.append(time.perf_counter() - t0)
+        finally:
+            if gc_was:
+                gc.enable()
+        e2e_s = max_over_ranks(sum(t), dist, dev)
+        e2e = {"value": round(world * a.f * n_e2e / e2e_s / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h_dim.numel() * 4 + 2 * a.f * 4), "d2h_bytes_per_step": 8 * 1000,
+               "ms_per_step": round(1e3 * e2e_s / n_e2e, 3), "steps": n_e2e,
+               "ms_each": [round(1e3 * x, 2) for x in t], "ms_median": round(1e3 * statistics.median(t), 3),
+               "python_gc": "collected before, disabled during the timed calls",
+               "api": "skx_join_aggregate_host (pinned host buffers; H2D, build, remap, reorder, probe, D2H)"}
+        del h_dim, h_fk, h_m
+
+
     # ---------------- roofline of the dominant kernel
     peak, peak_src = hbm_peak()
     D = expected_distinct(a.n, a.f, a.s)
@@ -615,47 +657,6 @@ def run_ours(a, rank, world, local_rank):
     if a.serve_n > 0 and rank == 0:
         serving = run_serving(a, dev)
         torch.cuda.empty_cache()
-
-    # ---------------- end to end through the host-buffer C-ABI call
-    e2e = None
-    if not a.no_e2e:
-        h_dim = torch.empty(w.dim.shape, dtype=torch.int32, pin_memory=True)
-        h_fk = torch.empty(a.f, dtype=torch.int32, pin_memory=True)
-        h_m = torch.empty(a.f, dtype=torch.int32, pin_memory=True)
-        h_dim.copy_(w.dim)
-        h_fk.copy_(w.fk)
-        h_m.copy_(w.measure)
-        h_out = np.zeros(1000, dtype=np.int64)
-        del fk2, dim2
-        torch.cuda.empty_cache()
-        skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
-        if not np.array_equal(h_out, result):
-            raise RuntimeError("host-buffer path disagrees with the device-resident path")
-        for _ in range(max(0, a.warmup - 1)):  # the checked call above is the first warm-up
-            skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
-        n_e2e = max(3, min(a.steps, 10))
-        # as timeit does: no cyclic garbage collection of the bench's own objects inside the
-        # timed calls (a full collection over this process's heap takes up to ~100 ms)
-        gc.collect()
-        gc_was = gc.isenabled()
-        gc.disable()
-        barrier()
-        t = []
-        try:
-            for _ in range(n_e2e):
-                t0 = time.perf_counter()
-                skx.skx_join_aggregate_host(h_dim, h_fk, h_m, q, out=h_out)
-                t.append(time.perf_counter() - t0)
-        finally:
-            if gc_was:
-                gc.enable()
-        e2e_s = max_over_ranks(sum(t), dist, dev)
-        e2e = {"value": round(world * a.f * n_e2e / e2e_s / 1e9, 3), "unit": UNIT,
-               "h2d_bytes_per_step": int(h_dim.numel() * 4 + 2 * a.f * 4), "d2h_bytes_per_step": 8 * 1000,
-               "ms_per_step": round(1e3 * e2e_s / n_e2e, 3), "steps": n_e2e,
-               "ms_each": [round(1e3 * x, 2) for x in t], "ms_median": round(1e3 * statistics.median(t), 3),
-               "python_gc": "collected before, disabled during the timed calls",
-               "api": "skx_join_aggregate_host (pinned host buffers; H2D, build, remap, reorder, probe, D2H)"}
 
     # ---------------- CPU baseline: the oracle on a bounded sample
     cpu = None
